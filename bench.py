@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 k-mer counter on the mid-size workload.
+
+One step = the whole hot path over one read set: 2-bit packing, signature
+scan, super k-mer binning, (k,x)-mer construction, radix sort, run-length
+counting with the cutoffs and the global order of the result
+(kmc_add_reads_device + kmc_count).  Workload: 50 Mbp order-3 Markov genome
+(GC 0.41) with 2,000 repeat copies of 5 kbp at 10 % divergence, 20 M reads
+of 150 bp, 0.5 % substitutions, 0.1 % N; k=28, m=7, 512 bins, cutoffs
+[2, 1e9].  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank counts its own copy of the workload
+(replicas; the path has no exchange step), value = all ranks' k-mers / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "k-mers counted/s at k=28 & % HBM roofline; batched/served vs plain; p99 latency"
+UNIT = "k-mers/s"
+WORKLOAD = ("mid: 50 Mbp order-3 Markov genome (GC 0.41) + 2,000 repeat copies of 5 kbp at 10% "
+            "divergence; 20M reads x 150 bp, 0.5% substitutions, 0.1% N; k=28, m=7, 512 bins, "
+            "cutoffs [2, 1e9]")
+CPU_SAMPLE_READS = 400_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def workload(scale):
+    from paper_1407_1507_gb300 import synth
+    return synth.mid(scale=scale)
+
+
+def cpu_baseline(w, k, ci, cx):
+    """The oracle as it stands on a bounded sample of the workload (host cores)."""
+    import oracle
+    n = min(CPU_SAMPLE_READS, w.n_reads)
+    b = w.bases[: int(w.offsets[n])]
+    o = w.offsets[: n + 1]
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    _, _, npos = oracle.count(b, o, k, ci, cx, threads=cores, return_npos=True)
+    dt = time.perf_counter() - t
+    return {"value": npos / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n:,} reads of the workload ({npos:,} k-mer positions), "
+                      f"{dt:.1f} s on {cores} host threads"}
+
+
+# Algorithmic bytes per launch of each stage (minimum traffic of the method:
+# every input read once, every output written once).
+def stage_bytes(st, k):
+    nb = st["n_bases"]
+    npos = st["n_kmer_positions"]
+    nrec = st["n_superkmers"]
+    binb = st["bin_bytes"]
+    nout = st["n_out"]
+    kw = 8 * ((k + 31) // 32)
+    return {
+        "pack": nb * 1.0 + nb / 4 + nb / 4,            # ASCII in; 2-bit codes + 2 masks out
+        "signature": nb / 4 + nb / 4 + 8 * nrec,        # codes + masks in; records out
+        "bin_scatter": 8 * nrec + binb / 2 + binb,      # records + bases in; bins out
+        "kx_count": binb,                               # bins in
+        "kx_scatter": binb + kw * npos,                 # bins in; keys out
+        "tile_sort": kw * npos + (kw + 4) * nout,       # keys in; survivors out
+        "order": 2 * (kw + 4) * nout,                   # survivors in and out
+    }
+
+
+def run_ours(args, rank, local_rank, world):
+    import torch
+    from paper_1407_1507_gb300 import kmc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload(args.scale)
+    k, m, B, ci, cx = w.k, w.m, w.n_bins, w.cutoff_min, w.cutoff_max
+    d_bases = torch.from_numpy(w.bases).to(dev)
+    d_offs = torch.from_numpy(w.offsets.view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = kmc.make_params(k, m=m, n_bins=B, cutoff_min=ci, cutoff_max=cx, device=local_rank,
+                        stream=stream.cuda_stream)
+    h = kmc.kmc_open(p)
+
+    def step():
+        kmc.kmc_reset(h)
+        kmc.kmc_add_reads_device(h, d_bases.data_ptr(), d_offs.data_ptr(), w.n_reads, w.bases.size)
+        kmc.kmc_count(h)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    st0 = kmc.kmc_stats_get(h)
+    npos = st0["n_kmer_positions"]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(local_rank)
+    clocks.start()
+    stage_ms = {s: 0.0 for s in kmc.STAGES}
+    launches = 0
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        st = kmc.kmc_stats_get(h)
+        for s, v in st["ms_stage"].items():
+            stage_ms[s] += v
+        launches += st["n_launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = npos * world / (ms / 1e3)
+
+    # roofline of the dominant kernel stage
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    per = {s: stage_ms[s] / args.steps for s in stage_ms}
+    alg = stage_bytes(st0, k)
+    dom = max((s for s in alg), key=lambda s: per.get(s, 0.0))
+    stages = {}
+    for s, b in alg.items():
+        if per.get(s, 0) > 0:
+            gbs = b / (per[s] / 1e3) / 1e9
+            stages[s] = {"ms": round(per[s], 4), "alg_bytes": int(b), "gbs": round(gbs, 1),
+                         "frac": round(gbs / peak, 4)}
+    achieved = stages[dom]["gbs"]
+    roofline = {"bound": "hbm", "kernel_stage": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.from_numpy(w.bases).pin_memory()
+        ho = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+        nout = st0["n_out"]
+        words = (k + 31) // 32
+        rk = torch.empty(max(nout, 1) * words, dtype=torch.int64).pin_memory()
+        rc = torch.empty(max(nout, 1), dtype=torch.int32).pin_memory()
+        import ctypes
+        lib = kmc.load()
+
+        def e2e_step():
+            kmc.kmc_reset(h)
+            kmc.kmc_add_reads_ptr(h, hb.data_ptr(), ho.data_ptr(), w.n_reads)
+            kmc.kmc_count(h)
+            n = ctypes.c_uint64()
+            r = lib.kmc_result(h, rk.data_ptr(), rc.data_ptr(), max(nout, 1), ctypes.byref(n))
+            if r != 0:
+                raise RuntimeError(kmc.strerror(r))
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": npos * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+               "h2d_bytes_per_step": int(w.bases.size + w.offsets.size * 8),
+               "d2h_bytes_per_step": int(nout * (8 * words + 4))}
+    kmc.kmc_close(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, k, ci, cx)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reads": w.n_reads, "bases": int(w.bases.size),
+                   "kmer_positions": npos, "result_kmers": st0["n_out"],
+                   "distinct_kmers": st0["n_distinct"], "super_kmers": st0["n_superkmers"],
+                   "x": st0["x_used"], "l2": "inputs (3 GB of reads, 19 GB of keys) exceed L2; no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "scale": args.scale},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "stages": stages,
+        "cpu_baseline": cpu, "clocks": clk,
+    }
+    return out
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step counts a bounded
+    sample of the same workload."""
+    if rank != 0:
+        return None
+    w = workload(args.scale)
+    import oracle
+    n = min(CPU_SAMPLE_READS, w.n_reads)
+    b = w.bases[: int(w.offsets[n])]
+    o = w.offsets[: n + 1]
+    cores = os.cpu_count() or 1
+    for _ in range(max(args.warmup, 0)):
+        oracle.count(b, o, w.k, w.cutoff_min, w.cutoff_max, threads=cores)
+    t = time.perf_counter()
+    npos = 0
+    for _ in range(args.steps):
+        _, _, npos = oracle.count(b, o, w.k, w.cutoff_min, w.cutoff_max, threads=cores, return_npos=True)
+    dt = (time.perf_counter() - t) / args.steps
+    v = npos / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_reads": n, "kmer_positions": npos},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {n:,} reads of the workload per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_info()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, local_rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * kmc.h -- C ABI of a GB300 (sm_103a) k-mer counter built on the method of
+ * KMC 2 (Deorowicz, Kokot, Grabowski, Debudaj-Grabysz, "KMC 2: Fast and
+ * resource-frugal k-mer counting", arXiv 1407.1507).
+ *
+ * The problem (paper Sect. 1): given a collection of reads, report every
+ * canonical k-mer (Sect. 2.1: the smaller of a k-mer and its reverse
+ * complement under A < C < G < T) with its number of occurrences, keeping
+ * only the k-mers whose count n satisfies cutoff_min <= n <= cutoff_max
+ * (Sect. 2.5; Suppl. S1 options -ci, -cx).  Every step runs in CUDA kernels
+ * of this library: 2-bit packing, the signature scan (Sect. 2.2), super
+ * k-mer binning (Sect. 2.4, Fig. 1), (k,x)-mer construction (Sect. 2.3),
+ * radix sorting, expansion and run-length counting (Sect. 2.4, Fig. 2).
+ *
+ * Conventions (all calls):
+ *   - Return KMC_OK (0) on success, a negative KMC_E* code otherwise;
+ *     kmc_strerror() names it.  A handle whose call failed with
+ *     KMC_ECUDA, KMC_ETIMEOUT or KMC_ENOMEM must be closed.
+ *   - Bases: ASCII.  'A','C','G','T' are bases; ANY other byte (including
+ *     lower case and 'N') breaks the read there: no k-mer spans it, and no
+ *     k-mer spans two reads.  Reads shorter than k add nothing.
+ *   - A k-mer is returned as W = ceil(k/32) uint64 words, most significant
+ *     word first, its value right-aligned in the low 2k bits, the first
+ *     symbol most significant, A=0 C=1 G=2 T=3 (Suppl. S4 [map] coding).
+ *     The result is sorted ascending by that value, one count per k-mer.
+ *   - A handle is not thread safe; distinct handles may be used from
+ *     different threads.  All work of a handle is ordered on its stream.
+ *   - The library allocates its own device and pinned host memory
+ *     (cudaMallocAsync on the handle's stream) and frees it in kmc_close.
+ */
+#ifndef KMC_GB300_KMC_H
+#define KMC_GB300_KMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------- error codes */
+#define KMC_OK 0
+#define KMC_EINVAL (-1)    /* bad argument or parameter                     */
+#define KMC_ESTATE (-2)    /* call out of order (e.g. result before count)  */
+#define KMC_ENOMEM (-3)    /* device or pinned host allocation failed       */
+#define KMC_ECUDA (-4)     /* a CUDA call or kernel launch failed           */
+#define KMC_EOVERFLOW (-5) /* a count exceeds UINT32_MAX                    */
+#define KMC_ETRUNC (-6)    /* caller capacity too small; *n_out still set    */
+#define KMC_ETIMEOUT (-7)  /* a device-side bounded wait gave up            */
+#define KMC_EAGAIN (-8)    /* not ready yet (server poll)                   */
+#define KMC_EINPUT (-9)    /* malformed read offsets                         */
+
+#define KMC_AUTO 0xFFFFFFFFu
+#define KMC_MAX_K 64u
+#define KMC_MIN_M 3u
+#define KMC_MAX_M 11u
+
+/* ---------------------------------------------------------- parameters */
+typedef struct {
+  uint32_t k;          /* k-mer length, 1..64 (Suppl. S1 -k; default 25)           */
+  uint32_t m;          /* signature length, 3..11 and m < k (Sect. 2.2; Suppl.
+                          S1 -p gives 5..7, default 7).  Values m >= k are
+                          clamped to k-1 for k >= 4; k <= 3 uses no signature
+                          (one bin).                                          */
+  uint32_t n_bins;     /* number of bins, 1..65536 (Sect. 2.4 uses <= 512)        */
+  uint32_t x;          /* (k,x)-mer extension, 0..3, or KMC_AUTO (Sect. 2.3)      */
+  uint64_t cutoff_min; /* keep count >= cutoff_min (Suppl. S1 -ci; default 2)     */
+  uint64_t cutoff_max; /* keep count <= cutoff_max (Suppl. S1 -cx; default 1e9)   */
+  uint32_t canonical;  /* must be 1: canonical k-mers (Sect. 2.1)                 */
+  int32_t device;      /* CUDA device ordinal                                     */
+  void *cuda_stream;   /* cudaStream_t to run on, or NULL for a stream of the
+                          handle's own                                        */
+  uint32_t debug_flags;/* KMC_DEBUG_* bits: keep intermediates for inspection     */
+  uint32_t reserved0;  /* must be zero                                            */
+  uint64_t piece_bytes;/* reads are distributed in pieces of about this many
+                          bytes (0 = 1 GiB); bounds the distribution scratch,
+                          never changes the result                            */
+  uint64_t reserved[2];/* must be zero                                            */
+} kmc_params;
+
+/* Fills *p with the paper's defaults: k=25, m=7, 512 bins, x=KMC_AUTO,
+ * cutoffs [2, 1e9], canonical, device 0, own stream. */
+void kmc_default_params(kmc_params *p);
+
+/* ---------------------------------------------------------- statistics */
+typedef struct {
+  uint64_t n_reads;          /* reads added                                    */
+  uint64_t n_bases;          /* bytes added                                    */
+  uint64_t n_kmer_positions; /* valid k-mer positions (sum of all counts)      */
+  uint64_t n_superkmers;     /* super k-mers (Sect. 2.4)                       */
+  uint64_t n_sorted_keys;    /* (k,x)-mers sorted (Sect. 2.3)                  */
+  uint64_t n_distinct;       /* distinct canonical k-mers before cutoffs       */
+  uint64_t n_out;            /* k-mers in the result                           */
+  uint64_t max_bin_kmers;    /* k-mer positions in the largest bin             */
+  uint64_t bin_bytes;        /* bytes of super k-mer records in the bins       */
+  uint32_t x_used;           /* x chosen (resolves KMC_AUTO)                   */
+  uint32_t m_used;           /* signature length used                          */
+  uint32_t n_tiles;          /* sort tiles processed                           */
+  uint32_t n_big_tiles;      /* tiles too large for one CTA's shared memory    */
+  float ms_distribute;       /* device time: pack, signatures, binning         */
+  float ms_sort;             /* device time: (k,x)-mers, sort, count           */
+  float ms_order;            /* device time: global ordering of the result     */
+  float ms_total;            /* device time of the last kmc_count              */
+  /* device time per kernel stage (CUDA events on the handle's stream),
+   * summed since kmc_open / kmc_reset, in the KMC_STAGE_* order below */
+  float ms_stage[12];
+  uint64_t n_launches;       /* kernels launched since kmc_open / kmc_reset    */
+} kmc_stats;
+
+/* Stage indices of kmc_stats.ms_stage. */
+enum {
+  KMC_STAGE_PACK = 0,      /* 2-bit packing and read-start marks             */
+  KMC_STAGE_SIGNATURE,     /* signature scan, super k-mer list               */
+  KMC_STAGE_BIN_SCATTER,   /* super k-mer records into bins                  */
+  KMC_STAGE_BIN_MAP,       /* sample histogram and bin map                   */
+  KMC_STAGE_KX_COUNT,      /* (k,x)-mer digit histogram                      */
+  KMC_STAGE_PLAN,          /* scans and tile plan                            */
+  KMC_STAGE_KX_SCATTER,    /* (k,x)-mer keys into digit buckets              */
+  KMC_STAGE_TILE_SORT,     /* shared-memory radix sort + run-length count    */
+  KMC_STAGE_BIG_SORT,      /* buckets larger than a tile                     */
+  KMC_STAGE_ORDER,         /* global order of the counted k-mers             */
+  KMC_STAGE_OTHER,
+  KMC_N_STAGES
+};
+
+/* ---------------------------------------------------------- handle */
+typedef struct kmc_handle kmc_handle;
+
+/* Validates *p and creates a handle (device memory is allocated lazily).
+ * *h is set to NULL on failure.  Errors: KMC_EINVAL, KMC_ECUDA, KMC_ENOMEM. */
+int kmc_open(kmc_handle **h, const kmc_params *p);
+
+/* Adds reads held in HOST memory: read i is bases[offsets[i] .. offsets[i+1]),
+ * offsets has n_reads+1 non-decreasing entries and offsets[0] == 0.  The
+ * bytes are copied (through pinned staging buffers, overlapped with the
+ * distribution kernels) before the call returns, so the caller may free them
+ * at once.  May be called repeatedly before kmc_count; each call appends.
+ * Errors: KMC_EINVAL (NULL pointer with n_reads > 0), KMC_EINPUT (offsets
+ * not non-decreasing or not starting at 0), KMC_ESTATE (after kmc_count
+ * without kmc_reset), KMC_ENOMEM, KMC_ECUDA. */
+int kmc_add_reads(kmc_handle *h, const char *bases, const uint64_t *offsets, uint64_t n_reads);
+
+/* As kmc_add_reads, for reads already in DEVICE memory of the handle's
+ * device: d_bases has n_bases bytes, d_offsets n_reads+1 entries with
+ * d_offsets[0] == 0 and d_offsets[n_reads] == n_bases.  The buffers are
+ * only read, by kernels ordered on the handle's stream; they must stay valid
+ * until kmc_add_reads_device returns (it synchronises with its own work).
+ * Malformed offsets are detected on the device: KMC_EINPUT. */
+int kmc_add_reads_device(kmc_handle *h, const char *d_bases, const uint64_t *d_offsets,
+                         uint64_t n_reads, uint64_t n_bases);
+
+/* Runs the sorting phase over all reads added and keeps the result on the
+ * device.  Blocks until done.  May be called again (it recounts the same
+ * reads).  Errors: KMC_ESTATE (no kmc_add_reads since open/reset is fine:
+ * the result is empty), KMC_EOVERFLOW, KMC_ENOMEM, KMC_ECUDA, KMC_ETIMEOUT. */
+int kmc_count(kmc_handle *h);
+
+/* Number of k-mers in the result.  Errors: KMC_ESTATE before kmc_count. */
+int kmc_result_size(const kmc_handle *h, uint64_t *n);
+
+/* Copies the result to HOST buffers: kmers gets n*ceil(k/32) uint64 words,
+ * counts n uint32.  If capacity < n nothing is copied and KMC_ETRUNC is
+ * returned; *n_out is set to n in both cases.  Either buffer may be NULL to
+ * skip it.  Errors: KMC_ESTATE, KMC_ETRUNC, KMC_ECUDA. */
+int kmc_result(kmc_handle *h, uint64_t *kmers, uint32_t *counts, uint64_t capacity,
+               uint64_t *n_out);
+
+/* Device pointers to the result (owned by the handle, valid until the next
+ * kmc_count, kmc_reset or kmc_close): *d_kmers holds n*ceil(k/32) words
+ * laid out as in kmc_result, *d_counts n counts.  Errors: KMC_ESTATE. */
+int kmc_result_device(kmc_handle *h, const uint64_t **d_kmers, const uint32_t **d_counts,
+                      uint64_t *n);
+
+/* Statistics of the reads added and the last kmc_count. */
+int kmc_stats_get(const kmc_handle *h, kmc_stats *s);
+
+/* Forgets the reads and the result; keeps device allocations for reuse. */
+int kmc_reset(kmc_handle *h);
+
+/* Releases everything the handle owns.  NULL is a no-op. */
+void kmc_close(kmc_handle *h);
+
+/* Static string naming an error code. */
+const char *kmc_strerror(int code);
+
+/* ---------------------------------------------------------- bin map
+ * Sect. 2.4: the 4^m signatures (plus the sentinel 4^m of k-mers with no
+ * allowed m-mer) are merged into n_bins bins from a signature histogram of
+ * a sample of the input.  By default the map is built on the device from
+ * the first kmc_add_reads call's reads (at most 2^20 of them): signatures
+ * sorted by sample weight, heaviest first (ties: smaller signature first),
+ * cut into consecutive groups of about total/n_bins weight; unseen
+ * signatures go to bin (signature mod n_bins).  The result never depends
+ * on the map.  kmc_set_bin_map replaces it (before the first
+ * kmc_add_reads): map has 4^m+1 entries, each < n_bins, in host memory,
+ * copied.  kmc_get_bin_map copies the map in use (after the first
+ * kmc_add_reads) to a host buffer of 4^m+1 entries.  Errors: KMC_EINVAL,
+ * KMC_ESTATE. */
+int kmc_set_bin_map(kmc_handle *h, const uint32_t *map, uint64_t n_entries);
+int kmc_get_bin_map(const kmc_handle *h, uint32_t *map, uint64_t n_entries);
+
+/* ---------------------------------------------------------- introspection
+ * Intermediate results, for checking each step against a CPU restatement.
+ *
+ * kmc_debug_superkmers: the super k-mers found by the signature scan
+ * (Sect. 2.4, Fig. 1) of all reads added, in no particular order: read
+ * index, position of the first k-mer in the read, number of k-mers and
+ * signature (4^m for none).  Super k-mers are maximal runs of consecutive
+ * valid k-mers with one signature, additionally cut before every k-mer whose
+ * position in its read is a multiple of 128 (a bound on record size; it does
+ * not change the result).  Needs KMC_DEBUG_KEEP_SUPERKMERS in
+ * params.debug_flags at open (keeps the list).  capacity < n: KMC_ETRUNC with *n_out = n.
+ *
+ * kmc_debug_bin_keys: after kmc_count, the sorted (k,x)-mer keys of one bin
+ * (Sect. 2.3): each key is ceil((2(k+x)+2)/64) words, most significant
+ * first; for x = 0 a key is the canonical k-mer value, for x > 0 it is
+ * [x' in the top 2 bits][the k+x' symbols of the stored (k,x)-mer,
+ * first symbol most significant, zero padded].  Needs KMC_DEBUG_KEEP_KEYS
+ * in params.debug_flags at open (keeps the sorted keys). */
+int kmc_debug_superkmers(kmc_handle *h, uint64_t *read_index, uint32_t *pos, uint32_t *n_kmers,
+                         uint32_t *sig, uint64_t capacity, uint64_t *n_out);
+int kmc_debug_bin_keys(kmc_handle *h, uint32_t bin, uint64_t *keys, uint64_t capacity,
+                       uint64_t *n_out, uint32_t *words_per_key);
+
+#define KMC_DEBUG_KEEP_SUPERKMERS 1u
+#define KMC_DEBUG_KEEP_KEYS 2u
+
+#ifdef __cplusplus
+}
+#endif
+#endif

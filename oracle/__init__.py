@@ -61,7 +61,7 @@ def _load():
         lib.oracle_position_sigs.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, u32p]
         lib.oracle_position_sigs.restype = None
         lib.oracle_superkmers.argtypes = [u8p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                          u64p, u32p, u32p, ctypes.c_uint64]
+                                          ctypes.c_uint32, u64p, u32p, u32p, ctypes.c_uint64]
         lib.oracle_superkmers.restype = ctypes.c_uint64
         lib.oracle_kxmers.argtypes = [intp, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, u64p, u32p,
                                       u32p, u64p, u64p, ctypes.c_uint64]
@@ -130,15 +130,17 @@ def position_sigs(bases, offsets, k, m):
     return out
 
 
-def superkmers(read, k, m, use_minimizer=False):
-    """Fig. 1 split of one read: list of (start, n_kmers, signature)."""
+def superkmers(read, k, m, use_minimizer=False, cut_every=0):
+    """Fig. 1 split of one read: list of (start, n_kmers, signature).
+
+    cut_every > 0 also cuts before read positions that are multiples of it."""
     lib = _load()
     b = np.frombuffer(read.encode() if isinstance(read, str) else bytes(read), dtype=np.uint8).copy()
     cap = max(1, b.size)
     st = np.zeros(cap, np.uint64)
     nk = np.zeros(cap, np.uint32)
     sg = np.zeros(cap, np.uint32)
-    n = lib.oracle_superkmers(_p(b, ctypes.c_uint8), b.size, k, m, int(use_minimizer),
+    n = lib.oracle_superkmers(_p(b, ctypes.c_uint8), b.size, k, m, int(use_minimizer), cut_every,
                               _p(st, ctypes.c_uint64), _p(nk, ctypes.c_uint32),
                               _p(sg, ctypes.c_uint32), cap)
     return [(int(st[i]), int(nk[i]), int(sg[i])) for i in range(n)]

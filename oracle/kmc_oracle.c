@@ -154,10 +154,12 @@ void oracle_position_sigs(const uint8_t *bases, const uint64_t *offsets, uint64_
  * k-mer writes its first k-mer's position in the read, its number of k-mers
  * and its signature.  Returns the number of super k-mers (at most `cap` are
  * written).  `use_minimizer` = 1 uses the canonical minimiser without the
- * Sect. 2.2 filter (Fig. 1, top), for comparison.
+ * Sect. 2.2 filter (Fig. 1, top), for comparison.  `cut_every` > 0 also
+ * starts a new super k-mer at every read position that is a multiple of it.
  */
 uint64_t oracle_superkmers(const uint8_t *read, uint64_t L, int k, int m, int use_minimizer,
-                           uint64_t *start, uint32_t *n_kmers, uint32_t *sig, uint64_t cap) {
+                           uint32_t cut_every, uint64_t *start, uint32_t *n_kmers, uint32_t *sig,
+                           uint64_t cap) {
   int *codes = (int *)malloc((L ? L : 1) * sizeof(int));
   codes_of(read, L, codes);
   uint64_t n = 0;
@@ -177,7 +179,11 @@ uint64_t oracle_superkmers(const uint8_t *read, uint64_t L, int k, int m, int us
     } else {
       s = oracle_signature(codes + p, k, m);
     }
-    if (open && s == cur) {
+    /* reading: a super k-mer may also be cut before every k-mer whose
+     * position in the read is a multiple of cut_every (0 = never); this bounds
+     * record sizes and leaves the counts unchanged. */
+    int cut = cut_every && (p % cut_every) == 0;
+    if (open && s == cur && !cut) {
       if (n - 1 < cap) n_kmers[n - 1] += 1;
     } else {
       if (n < cap) { start[n] = p; n_kmers[n] = 1; sig[n] = s; }

@@ -1,0 +1,146 @@
+// Host-side internals shared by the translation units of libkmc.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/kmc.h"
+
+namespace kmc {
+
+int cuda_fail(cudaError_t e, const char *what);
+extern thread_local uint64_t g_launches;
+
+// Stream-ordered device buffer that only grows (reused across calls).
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+int dev_ensure(DevBuf &b, size_t bytes, cudaStream_t st);
+void dev_release(DevBuf &b, cudaStream_t st);
+
+template <typename T>
+inline T *as(DevBuf &b) { return static_cast<T *>(b.p); }
+
+// One piece of input after the distribution phase: its super k-mer records,
+// grouped by bin.  index[i] = word offset (bits 63..32) | n_kmers-1 (bits
+// 31..25) | signature (bits 24..0); words = packed bases of the records.
+struct Piece {
+  DevBuf index;        // uint64[n_records]
+  DevBuf words;        // uint64[n_words + pad]
+  DevBuf rec_base;     // uint64[B+1]: first record of each bin
+  uint64_t n_records = 0;
+  uint64_t n_words = 0;
+  uint64_t n_kmers = 0;
+  // kept only with KMC_DEBUG_KEEP_SUPERKMERS: the raw super k-mer list
+  DevBuf dbg_list;     // uint64[n_records]: stream position (hi 32) | n_sig (lo 32)
+  DevBuf dbg_read;     // uint64[n_records]: read index
+  DevBuf dbg_rel;      // uint32[n_records]: position in read
+};
+
+// Per-call scratch of the distribution phase (reused).
+struct DistScratch {
+  DevBuf packed, inval, starts;  // bit streams of the current piece
+  DevBuf list;                   // uint64 super k-mer list
+  DevBuf counters;               // device counters
+  DevBuf hist;                   // per-bin histograms (records, words, kmers)
+  DevBuf scan_tmp, bin_scan;
+  DevBuf stage_dev[2];           // device staging of host reads
+  DevBuf offs_dev[2];
+  void *stage_host[2] = {nullptr, nullptr};
+  size_t stage_host_cap[2] = {0, 0};
+  cudaEvent_t stage_free[2] = {nullptr, nullptr};
+};
+
+// Per-call scratch of the sorting phase.
+struct SortScratch {
+  DevBuf hist, bucket_base, cursor, flags, flag_scan, tile_first, scan_tmp;
+  DevBuf keys, sorted_keys, big_list, big_scratch;
+  DevBuf sv_keys, sv_counts;  // survivors before global order
+  DevBuf counters;
+  // global-order pass
+  DevBuf o_hist, o_base, o_cursor, o_flags, o_flag_scan, o_tile_first, o_scan_tmp, o_big_list,
+      o_big_k, o_big_v;
+};
+
+// Device time per stage: events recorded around launches on the handle's
+// stream, resolved after the stream has been synchronised.
+struct StageTimer {
+  struct Rec { int stage; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  float ms[KMC_N_STAGES] = {};
+  uint64_t launches = 0;
+  cudaEvent_t get();
+  size_t begin(int stage, cudaStream_t st);
+  void end(size_t idx, cudaStream_t st);
+  void resolve();   // call after a stream synchronise
+  void destroy();
+  void clear();
+};
+
+struct Handle {
+  kmc_params p{};
+  uint32_t m_used = 0;
+  uint64_t piece_bytes = 0;
+  uint32_t n_sig = 0;          // 4^m_used + 1 signatures (the last is "none")
+  int key_words = 1;           // 64-bit words per k-mer in the result
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  DevBuf err;                  // uint32 device error word
+  DevBuf map;                  // uint32[n_sig] signature -> bin
+  bool map_ready = false;
+  bool map_user = false;
+  std::vector<Piece *> pieces;
+  DistScratch ds;
+  SortScratch ss;
+  // result
+  DevBuf out_kmers, out_counts;
+  uint64_t n_out = 0;
+  bool counted = false;
+  // statistics
+  kmc_stats stats{};
+  std::vector<uint64_t> bin_kmers;   // k-mer positions per bin (all pieces)
+  cudaEvent_t ev[8] = {};
+  StageTimer timer;
+};
+
+// Brackets a launch: STAGE(h, KMC_STAGE_X) { kernel<<<...>>>(...); }
+struct StageScope {
+  Handle &h;
+  size_t idx;
+  StageScope(Handle &hh, int stage) : h(hh), idx(hh.timer.begin(stage, hh.st)) {}
+  ~StageScope() { h.timer.end(idx, h.st); }
+};
+
+// Adds the kernels launched by this thread during a call to the handle.
+struct LaunchScope {
+  Handle &h;
+  uint64_t l0;
+  explicit LaunchScope(Handle &hh) : h(hh), l0(g_launches) {}
+  ~LaunchScope() { h.timer.launches += g_launches - l0; }
+};
+
+// distribute.cu
+int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_offsets,
+                            uint64_t n_reads, uint64_t byte_start, uint64_t byte_end,
+                            uint64_t read_base);
+int build_bin_map(Handle &h, const char *piece_ptr, const uint64_t *d_offsets, uint64_t n_reads,
+                  uint64_t byte_start, uint64_t byte_end, uint64_t read_base);
+int debug_superkmers(Handle &h, uint64_t *read_index, uint32_t *pos, uint32_t *n_kmers,
+                     uint32_t *sig, uint64_t capacity, uint64_t *n_out);
+
+// count.cu
+int sort_phase(Handle &h);
+int debug_bin_keys(Handle &h, uint32_t bin, uint64_t *keys, uint64_t capacity, uint64_t *n_out,
+                   uint32_t *words_per_key);
+
+// order.cu: sort (key, value) pairs in place by key bits [0, key_bits)
+int sort_pairs_u64(Handle &h, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits);
+int sort_pairs_u128(Handle &h, unsigned __int128 *keys, uint32_t *vals, uint64_t n, int key_bits);
+
+int check_device_error(Handle &h);
+
+}  // namespace kmc

@@ -1,0 +1,619 @@
+// Radix-sort machinery of the sorting phase (paper Sect. 2.4: "performs
+// radix sort algorithm on them").
+//
+// Design (GB300-first).  A bin's keys are first scattered by their top D
+// bits into digit buckets (an MSD step done by the key-building kernel);
+// consecutive buckets are packed into tiles of at most TILE keys; each tile
+// is then sorted entirely in shared memory by an LSD radix sort with 8-bit
+// digits over the bits that vary inside the tile, so every key crosses HBM
+// once in and once out.  Ranking inside a pass uses warp match (all lanes
+// with equal digits find each other in one instruction) and per-warp digit
+// counters in shared memory, scanned block-wide in (digit, warp) order,
+// which keeps every pass stable.  A bucket larger than a tile (e.g. one
+// k-mer repeated millions of times) takes a slower path: one CTA sorts it
+// with LSD passes through global memory.
+#pragma once
+#include <type_traits>
+#include "common.cuh"
+
+namespace kmc {
+
+struct NoVal {};
+
+// ---------------------------------------------------------------- scans
+
+// Inclusive warp scan.
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T o = __shfl_up_sync(FULL, v, d);
+    if (lane >= (unsigned)d) v += o;
+  }
+  return v;
+}
+
+// Exclusive block scan of one value per thread; returns the exclusive prefix
+// and writes the block total to *total.  `ws` holds THREADS/32 + 1 entries.
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_excl_scan(T v, T *ws, T *total) {
+  constexpr int NW = THREADS / 32;
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T x = lane < (unsigned)NW ? ws[lane] : T(0);
+    T xi = warp_incl_scan(x);
+    if (lane < (unsigned)NW) ws[lane] = xi - x;
+    if (lane == NW - 1) ws[NW] = xi;
+  }
+  __syncthreads();
+  T r = ws[w] + inc - v;
+  *total = ws[NW];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------ block radix sort
+
+// Sorts THREADS*IPT keys (plus optional payload) held in registers in the
+// warp-striped arrangement: element e = warp*32*IPT + i*32 + lane sits in
+// keys[i] of that lane.  Sorts on bits [0, nbits).  On return the sorted
+// keys are in smem.keys (and smem.vals), in order.
+template <typename K, typename V, int THREADS, int IPT>
+struct BlockSort {
+  static constexpr int NW = THREADS / 32;
+  static constexpr int TILE = THREADS * IPT;
+  static constexpr bool HAS_V = !std::is_same<V, NoVal>::value;
+  static_assert(NW >= 8 && (NW % 8) == 0, "THREADS must be a multiple of 256");
+  struct Smem {
+    K keys[TILE];
+    typename std::conditional<HAS_V, V, char>::type vals[HAS_V ? TILE : 1];
+    uint32_t cnt[NW][256];
+    uint32_t ws[NW + 1];
+  };
+
+  __device__ static void sort(K (&k)[IPT], V (&v)[IPT], int nbits, Smem &s) {
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    for (int bit = 0; bit < nbits; bit += 8) {
+      const int nb = nbits - bit < 8 ? nbits - bit : 8;
+      for (int i = lane; i < 256; i += 32) s.cnt[w][i] = 0;
+      __syncwarp();
+      uint32_t rank[IPT];
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        unsigned d = KeyTraits<K>::digit(k[i], bit, nb);
+        unsigned peers = __match_any_sync(FULL, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if ((int)lane == leader) {
+          base = s.cnt[w][d];
+          s.cnt[w][d] = base + __popc(peers);
+        }
+        base = __shfl_sync(FULL, base, leader);
+        rank[i] = base + __popc(peers & lanemask_lt());
+        __syncwarp();
+      }
+      __syncthreads();
+      // Exclusive scan of the counters in (digit, warp) order: thread t owns
+      // digit t/(NW/8) and warps (t%(NW/8))*8 .. +8.
+      {
+        const int d = threadIdx.x / (NW / 8);
+        const int w0 = (threadIdx.x % (NW / 8)) * 8;
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { c[j] = s.cnt[w0 + j][d]; sum += c[j]; }
+        uint32_t total;
+        uint32_t pre = block_excl_scan<uint32_t, THREADS>(sum, s.ws, &total);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { s.cnt[w0 + j][d] = pre; pre += c[j]; }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        unsigned d = KeyTraits<K>::digit(k[i], bit, nb);
+        uint32_t pos = s.cnt[w][d] + rank[i];
+        s.keys[pos] = k[i];
+        if constexpr (HAS_V) s.vals[pos] = v[i];
+      }
+      __syncthreads();
+      if (bit + 8 < nbits) {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+          int e = w * 32 * IPT + i * 32 + lane;
+          k[i] = s.keys[e];
+          if constexpr (HAS_V) v[i] = s.vals[e];
+        }
+        __syncthreads();
+      }
+    }
+    if (nbits <= 0) {  // nothing to sort: still leave the keys in smem, in order
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        int e = w * 32 * IPT + i * 32 + lane;
+        s.keys[e] = k[i];
+        if constexpr (HAS_V) s.vals[e] = v[i];
+      }
+      __syncthreads();
+    }
+  }
+};
+
+// Bits that vary inside a tile whose keys share the top `D` digit bits in
+// [d_first, d_last] and have `key_bits` significant bits.
+__host__ __device__ __forceinline__ int tile_sort_bits(int key_bits, int D, uint32_t d_first,
+                                                       uint32_t d_last) {
+  uint32_t x = d_first ^ d_last;
+  int diff = 0;
+  while (x) { ++diff; x >>= 1; }
+  return key_bits - D + diff;
+}
+
+// ------------------------------------------------------ tile descriptors
+// A tile plan over digit buckets: buckets (group g, digit d) flattened as
+// g*ND + d, bucket_base[i] = first key of bucket i (exclusive scan of the
+// counts, with bucket_base[G*ND] = total).  tile_first[t] = flattened index
+// of the first bucket of tile t; the tile ends where tile t+1 begins (or at
+// the end of its group).
+struct TilePlan {
+  const uint64_t *bucket_base;  // [G*ND + 1]
+  const uint32_t *tile_first;   // [n_tiles]
+  const uint32_t *n_tiles;      // device scalar
+  uint32_t ND;                  // digits per group (2^D)
+  int D;
+  int key_bits;
+};
+
+__device__ __forceinline__ void tile_range(const TilePlan &p, uint32_t t, uint32_t nt,
+                                           uint64_t *start, uint64_t *end, uint32_t *dfirst,
+                                           uint32_t *dlast) {
+  uint32_t i = p.tile_first[t];
+  uint32_t g = i / p.ND;
+  uint32_t inext = (t + 1 < nt) ? p.tile_first[t + 1] : 0xFFFFFFFFu;
+  uint32_t gend = (g + 1) * p.ND;
+  uint32_t j = (inext < gend) ? inext : gend;  // one past the tile's last bucket
+  *start = p.bucket_base[i];
+  *end = p.bucket_base[j];
+  *dfirst = i - g * p.ND;
+  *dlast = j - 1 - g * p.ND;
+}
+
+// ---------------------------------------------------------------- tile kernels
+
+// Grabs the next tile index for the whole CTA (persistent-CTA work loop).
+__device__ __forceinline__ uint32_t next_tile(uint32_t *work, uint32_t *s_tile) {
+  if (threadIdx.x == 0) *s_tile = atomicAdd(work, 1u);
+  __syncthreads();
+  uint32_t t = *s_tile;
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ void push_big(uint32_t t, uint64_t n, uint32_t *big_list,
+                                         uint32_t *n_big, unsigned long long *big_keys,
+                                         uint32_t big_cap, uint32_t *err) {
+  uint32_t idx = atomicAdd(n_big, 1u);
+  if (idx < big_cap) {
+    big_list[idx] = t;
+    atomicAdd(big_keys, (unsigned long long)n);
+  } else {
+    atomicOr(err, ERR_CAPACITY);
+  }
+}
+
+// Output of run-length counting: the survivors of a tile, sorted.
+template <typename K>
+struct CountOut {
+  K *keys;                     // survivor k-mers
+  uint32_t *counts;            // their counts
+  unsigned long long *n;       // survivors written so far (device counter)
+  uint64_t cap;                // capacity of keys/counts
+  uint64_t ci, cx;             // inclusive cutoffs (Sect. 2.5)
+  unsigned long long *n_distinct;
+};
+
+// Sect. 2.4 "calculates the statistics": run-length count of the sorted keys
+// s_keys[0..n) of one tile, keep counts in [ci, cx], append to `out`.
+template <typename K, int THREADS, int IPT>
+__device__ void tile_rle(const K *s_keys, int n, uint16_t *heads, uint32_t *ws,
+                         unsigned long long *s_base, const CountOut<K> &out, uint32_t *err) {
+  const int e0 = threadIdx.x * IPT;
+  uint32_t nh = 0;
+#pragma unroll 4
+  for (int j = 0; j < IPT; ++j) {
+    int e = e0 + j;
+    if (e < n && (e == 0 || s_keys[e] != s_keys[e - 1])) ++nh;
+  }
+  uint32_t U;
+  uint32_t hb = block_excl_scan<uint32_t, THREADS>(nh, ws, &U);
+#pragma unroll 4
+  for (int j = 0; j < IPT; ++j) {
+    int e = e0 + j;
+    if (e < n && (e == 0 || s_keys[e] != s_keys[e - 1])) heads[hb++] = (uint16_t)e;
+  }
+  if (threadIdx.x == 0) heads[U] = (uint16_t)n;
+  __syncthreads();
+  const uint32_t Q = (U + THREADS - 1) / THREADS;
+  const uint32_t u0 = threadIdx.x * Q;
+  uint32_t keep = 0;
+  for (uint32_t j = 0; j < Q; ++j) {
+    uint32_t u = u0 + j;
+    if (u < U) {
+      uint32_t c = (uint32_t)heads[u + 1] - heads[u];
+      keep += (c >= out.ci && c <= out.cx);
+    }
+  }
+  uint32_t ktot;
+  uint32_t kb = block_excl_scan<uint32_t, THREADS>(keep, ws, &ktot);
+  if (threadIdx.x == 0) {
+    *s_base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
+    atomicAdd(out.n_distinct, (unsigned long long)U);
+  }
+  __syncthreads();
+  const uint64_t base = *s_base;
+  if (base + ktot > out.cap) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_CAPACITY);
+  } else {
+    for (uint32_t j = 0; j < Q; ++j) {
+      uint32_t u = u0 + j;
+      if (u < U) {
+        uint32_t h = heads[u];
+        uint32_t c = (uint32_t)heads[u + 1] - h;
+        if (c >= out.ci && c <= out.cx) {
+          out.keys[base + kb] = s_keys[h];
+          out.counts[base + kb] = c;
+          ++kb;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename K, int THREADS, int IPT>
+struct TileCountSmem {
+  typename BlockSort<K, NoVal, THREADS, IPT>::Smem bs;
+  uint16_t heads[THREADS * IPT + 1];
+  uint32_t tile;
+  unsigned long long base;
+};
+
+// Count mode: sort every tile of the plan and run-length count it (x = 0:
+// the keys are canonical k-mers).  Tiles above one CTA's capacity are put on
+// the big list.  If `sorted_out` is not NULL the sorted keys are also
+// written back there (inspection).
+template <typename K, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<K> out,
+                  uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys,
+                  uint32_t big_cap, uint32_t *err, K *sorted_out) {
+  using BS = BlockSort<K, NoVal, THREADS, IPT>;
+  using SM = TileCountSmem<K, THREADS, IPT>;
+  static_assert(BS::TILE < 65536, "heads are 16-bit");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t nt = *plan.n_tiles;
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  for (;;) {
+    const uint32_t t = next_tile(work, &sm.tile);
+    if (t >= nt) break;
+    uint64_t st, en;
+    uint32_t d0, d1;
+    tile_range(plan, t, nt, &st, &en, &d0, &d1);
+    const uint64_t n64 = en - st;
+    if (n64 == 0) continue;
+    if (n64 > (uint64_t)BS::TILE) {
+      if (threadIdx.x == 0) push_big(t, n64, big_list, n_big, big_keys, big_cap, err);
+      continue;
+    }
+    const int n = (int)n64;
+    K k[IPT];
+    NoVal v[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      int e = w * 32 * IPT + i * 32 + lane;
+      k[i] = e < n ? keys[st + e] : KeyTraits<K>::max_key();
+    }
+    BS::sort(k, v, tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm.bs);
+    if (sorted_out)
+      for (int e = threadIdx.x; e < n; e += THREADS) sorted_out[st + e] = sm.bs.keys[e];
+    tile_rle<K, THREADS, IPT>(sm.bs.keys, n, sm.heads, sm.bs.ws, &sm.base, out, err);
+  }
+}
+
+// Pairs mode: sort every tile of (key, value) pairs in place (keys/vals are
+// read and written at the same positions).  Used to put the survivors in
+// global order and to order signatures by weight.
+template <typename K, typename V, int THREADS, int IPT>
+struct TilePairsSmem {
+  typename BlockSort<K, V, THREADS, IPT>::Smem bs;
+  uint32_t tile;
+};
+
+template <typename K, typename V, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+tile_pairs_kernel(K *keys, V *vals, TilePlan plan, uint32_t *work, uint32_t *big_list,
+                  uint32_t *n_big, unsigned long long *big_keys, uint32_t big_cap,
+                  uint32_t *err) {
+  using BS = BlockSort<K, V, THREADS, IPT>;
+  using SM = TilePairsSmem<K, V, THREADS, IPT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t nt = *plan.n_tiles;
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  for (;;) {
+    const uint32_t t = next_tile(work, &sm.tile);
+    if (t >= nt) break;
+    uint64_t st, en;
+    uint32_t d0, d1;
+    tile_range(plan, t, nt, &st, &en, &d0, &d1);
+    const uint64_t n64 = en - st;
+    if (n64 <= 1) continue;
+    if (n64 > (uint64_t)BS::TILE) {
+      if (threadIdx.x == 0) push_big(t, n64, big_list, n_big, big_keys, big_cap, err);
+      continue;
+    }
+    const int n = (int)n64;
+    K k[IPT];
+    V v[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      int e = w * 32 * IPT + i * 32 + lane;
+      k[i] = e < n ? keys[st + e] : KeyTraits<K>::max_key();
+      v[i] = e < n ? vals[st + e] : V();
+    }
+    BS::sort(k, v, tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm.bs);
+    for (int e = threadIdx.x; e < n; e += THREADS) {
+      keys[st + e] = sm.bs.keys[e];
+      vals[st + e] = sm.bs.vals[e];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- big tiles
+// One CTA per bucket larger than a tile: LSD passes (8-bit digits) through
+// global memory with a scratch buffer; each pass is a digit histogram, a
+// scan, and a stable chunked scatter.  A pass whose digit is the same for
+// every key is skipped (all-identical buckets cost one histogram per pass).
+
+template <typename K, typename V, int THREADS, int IPT>
+struct BigSmem {
+  static constexpr int NW = THREADS / 32;
+  static constexpr int CH = THREADS * IPT;
+  uint32_t cnt[NW][257];
+  unsigned long long offs[257];
+  uint32_t ws[NW + 1];
+  uint32_t pos[CH];
+  uint32_t flag;
+  unsigned long long base;
+};
+
+// Sorts src[0..n) (+ payload) on bits [0, nbits); returns the buffer that
+// holds the result (src or dst).
+template <typename K, typename V, int THREADS, int IPT>
+__device__ bool big_sort(K *src_k, V *src_v, K *dst_k, V *dst_v, uint64_t n, int nbits,
+                         BigSmem<K, V, THREADS, IPT> &sm) {
+  constexpr bool HAS_V = !std::is_same<V, NoVal>::value;
+  constexpr int NW = THREADS / 32, CH = THREADS * IPT;
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  bool in_dst = false;
+  for (int bit = 0; bit < nbits; bit += 8) {
+    const int nb = nbits - bit < 8 ? nbits - bit : 8;
+    K *sk = in_dst ? dst_k : src_k;
+    V *sv = in_dst ? dst_v : src_v;
+    K *dk = in_dst ? src_k : dst_k;
+    V *dv = in_dst ? src_v : dst_v;
+    // histogram (warp-aggregated)
+    for (int i = threadIdx.x; i < 257; i += THREADS) sm.offs[i] = 0;
+    __syncthreads();
+    for (uint64_t e = threadIdx.x; e < n + (THREADS - 1) - ((n + THREADS - 1) % THREADS) ; e += THREADS) {
+      unsigned d = e < n ? KeyTraits<K>::digit(sk[e], bit, nb) : 256u;
+      unsigned peers = __match_any_sync(FULL, d);
+      if (d < 256u && (int)lane == __ffs(peers) - 1) atomicAdd(&sm.offs[d], (unsigned long long)__popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long acc = 0;
+      uint32_t single = 0;
+      for (int d = 0; d < 256; ++d) {
+        unsigned long long c = sm.offs[d];
+        if (c == n) single = 1;
+        sm.offs[d] = acc;
+        acc += c;
+      }
+      sm.flag = single;
+    }
+    __syncthreads();
+    if (sm.flag) continue;  // every key has this digit: the pass is the identity
+    for (uint64_t c0 = 0; c0 < n; c0 += CH) {
+      for (int i = lane; i < 257; i += 32) sm.cnt[w][i] = 0;
+      __syncwarp();
+      K k[IPT];
+      V v[IPT];
+      unsigned dg[IPT];
+      uint32_t rank[IPT];
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        uint64_t e = c0 + w * 32 * IPT + i * 32 + lane;
+        bool ok = e < n;
+        k[i] = ok ? sk[e] : KeyTraits<K>::max_key();
+        if constexpr (HAS_V) v[i] = ok ? sv[e] : V();
+        dg[i] = ok ? KeyTraits<K>::digit(k[i], bit, nb) : 256u;
+        unsigned peers = __match_any_sync(FULL, dg[i]);
+        int leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if ((int)lane == leader) {
+          b = sm.cnt[w][dg[i]];
+          sm.cnt[w][dg[i]] = b + __popc(peers);
+        }
+        b = __shfl_sync(FULL, b, leader);
+        rank[i] = b + __popc(peers & lanemask_lt());
+        __syncwarp();
+      }
+      __syncthreads();
+      // per digit: exclusive prefix over warps, then add the running offset
+      for (int d = threadIdx.x; d < 256; d += THREADS) {
+        uint32_t acc = 0;
+        for (int ww = 0; ww < NW; ++ww) {
+          uint32_t c = sm.cnt[ww][d];
+          sm.cnt[ww][d] = acc;
+          acc += c;
+        }
+        sm.pos[d] = acc;  // chunk total of digit d (pos[] reused as scratch)
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        if (dg[i] < 256u) {
+          unsigned long long p = sm.offs[dg[i]] + sm.cnt[w][dg[i]] + rank[i];
+          dk[p] = k[i];
+          if constexpr (HAS_V) dv[p] = v[i];
+        }
+      }
+      __syncthreads();
+      for (int d = threadIdx.x; d < 256; d += THREADS) sm.offs[d] += sm.pos[d];
+      __syncthreads();
+    }
+    in_dst = !in_dst;
+  }
+  return in_dst;
+}
+
+// Count mode big tiles: sort (in place + scratch), then run-length count
+// chunk by chunk, carrying the open run across chunks.
+template <typename K, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
+                 unsigned long long *scratch_cursor, CountOut<K> out, uint32_t *err) {
+  using SM = BigSmem<K, NoVal, THREADS, IPT>;
+  constexpr int CH = THREADS * IPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t t = big_list[blockIdx.x];
+  const uint32_t nt = *plan.n_tiles;
+  uint64_t st, en;
+  uint32_t d0, d1;
+  tile_range(plan, t, nt, &st, &en, &d0, &d1);
+  const uint64_t n = en - st;
+  if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
+  __syncthreads();
+  K *sc = scratch + sm.base;
+  const bool in_scratch = big_sort<K, NoVal, THREADS, IPT>(keys + st, (NoVal *)nullptr, sc,
+                                                           (NoVal *)nullptr, n,
+                                                           tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm);
+  const K *a = in_scratch ? sc : keys + st;
+  // heads: run starts; the run open at the end of a chunk continues in the next
+  uint64_t open = 0;  // start of the open run (element 0 always starts one)
+  uint32_t *ws = sm.ws;
+  unsigned long long n_runs = 0;
+  for (uint64_t c0 = 0; c0 < n; c0 += CH) {
+    // compact head positions of this chunk (excluding element 0, the first open run)
+    uint32_t nh = 0;
+    const uint64_t e0 = c0 + (uint64_t)threadIdx.x * IPT;
+    for (int j = 0; j < IPT; ++j) {
+      uint64_t e = e0 + j;
+      if (e < n && e > 0 && a[e] != a[e - 1]) ++nh;
+    }
+    uint32_t tot;
+    uint32_t hb = block_excl_scan<uint32_t, THREADS>(nh, ws, &tot);
+    for (int j = 0; j < IPT; ++j) {
+      uint64_t e = e0 + j;
+      if (e < n && e > 0 && a[e] != a[e - 1]) sm.pos[hb++] = (uint32_t)(e - c0);
+    }
+    __syncthreads();
+    // runs closed in this chunk: [prev, pos[0]), [pos[0], pos[1]), ...; plus the
+    // final run when this is the last chunk.
+    const bool last = c0 + CH >= n;
+    const uint32_t nclosed = tot + (last ? 1u : 0u);
+    uint32_t keep = 0;
+    const uint32_t Q = (nclosed + THREADS - 1) / THREADS;
+    const uint32_t r0 = threadIdx.x * Q;
+    for (uint32_t j = 0; j < Q; ++j) {
+      uint32_t r = r0 + j;
+      if (r < nclosed) {
+        uint64_t rs = r == 0 ? open : c0 + sm.pos[r - 1];
+        uint64_t re = r < tot ? c0 + sm.pos[r] : n;
+        uint64_t c = re - rs;
+        if (c > 0xFFFFFFFFull && c >= out.ci && c <= out.cx) atomicOr(err, ERR_OVERFLOW);
+        keep += (c >= out.ci && c <= out.cx && c <= 0xFFFFFFFFull);
+      }
+    }
+    uint32_t ktot;
+    uint32_t kb = block_excl_scan<uint32_t, THREADS>(keep, ws, &ktot);
+    if (threadIdx.x == 0) sm.base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
+    __syncthreads();
+    const uint64_t base = sm.base;
+    if (base + ktot > out.cap) {
+      if (threadIdx.x == 0) atomicOr(err, ERR_CAPACITY);
+    } else {
+      for (uint32_t j = 0; j < Q; ++j) {
+        uint32_t r = r0 + j;
+        if (r < nclosed) {
+          uint64_t rs = r == 0 ? open : c0 + sm.pos[r - 1];
+          uint64_t re = r < tot ? c0 + sm.pos[r] : n;
+          uint64_t c = re - rs;
+          if (c >= out.ci && c <= out.cx && c <= 0xFFFFFFFFull) {
+            out.keys[base + kb] = a[rs];
+            out.counts[base + kb] = (uint32_t)c;
+            ++kb;
+          }
+        }
+      }
+    }
+    n_runs += nclosed;
+    if (tot) open = c0 + sm.pos[tot - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out.n_distinct, n_runs);
+}
+
+// Pairs mode big tiles: sort; copy back if the result ended in scratch.
+template <typename K, typename V, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, K *scratch_k,
+                 V *scratch_v, unsigned long long *scratch_cursor) {
+  using SM = BigSmem<K, V, THREADS, IPT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t t = big_list[blockIdx.x];
+  const uint32_t nt = *plan.n_tiles;
+  uint64_t st, en;
+  uint32_t d0, d1;
+  tile_range(plan, t, nt, &st, &en, &d0, &d1);
+  const uint64_t n = en - st;
+  if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
+  __syncthreads();
+  K *sk = scratch_k + sm.base;
+  V *sv = scratch_v + sm.base;
+  if (big_sort<K, V, THREADS, IPT>(keys + st, vals + st, sk, sv, n,
+                                   tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm)) {
+    for (uint64_t e = threadIdx.x; e < n; e += THREADS) {
+      keys[st + e] = sk[e];
+      vals[st + e] = sv[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- plan kernels
+
+// flag[i] = 1 where a tile starts (see plan_tiles in sortlib.cu for the rule).
+__global__ void plan_flags_kernel(const uint32_t *cnt, const uint64_t *base, uint64_t nbk,
+                                  uint32_t ND, uint32_t tile_cap, uint32_t *flag);
+__global__ void plan_emit_kernel(const uint32_t *flag, const uint64_t *flag_scan, uint64_t nbk,
+                                 uint32_t *tile_first, uint32_t *n_tiles);
+
+// ---------------------------------------------------------------- host API
+struct DeviceArena;  // defined in api
+
+// Exclusive scan of n values (uint32 or uint64 input) into uint64 out[n+1]
+// (out[n] = total).  `tmp` must hold scan_tmp_words(n) uint64 words.
+size_t scan_tmp_words(uint64_t n);
+cudaError_t device_excl_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t *tmp,
+                                 cudaStream_t st);
+cudaError_t device_excl_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, uint64_t *tmp,
+                                 cudaStream_t st);
+
+}  // namespace kmc

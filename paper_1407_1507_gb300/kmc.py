@@ -1,0 +1,307 @@
+"""Thin ctypes binding of libkmc (include/kmc.h): same names, argument
+marshalling only.  Every step of the counting runs in the library's CUDA
+kernels; there is no CPU fallback.  If libkmc.so is missing or cannot be
+loaded, import-time calls raise.
+
+Host inputs are numpy arrays (or anything exposing the buffer protocol);
+device inputs are torch CUDA tensors (only their data pointers are used).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KMC_OK = 0
+KMC_EINVAL = -1
+KMC_ESTATE = -2
+KMC_ENOMEM = -3
+KMC_ECUDA = -4
+KMC_EOVERFLOW = -5
+KMC_ETRUNC = -6
+KMC_ETIMEOUT = -7
+KMC_EAGAIN = -8
+KMC_EINPUT = -9
+KMC_AUTO = 0xFFFFFFFF
+KMC_DEBUG_KEEP_SUPERKMERS = 1
+KMC_DEBUG_KEEP_KEYS = 2
+
+
+class kmc_params(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_uint32), ("m", ctypes.c_uint32), ("n_bins", ctypes.c_uint32),
+        ("x", ctypes.c_uint32), ("cutoff_min", ctypes.c_uint64), ("cutoff_max", ctypes.c_uint64),
+        ("canonical", ctypes.c_uint32), ("device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+        ("debug_flags", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+        ("piece_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2),
+    ]
+
+
+class kmc_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_reads", ctypes.c_uint64), ("n_bases", ctypes.c_uint64),
+        ("n_kmer_positions", ctypes.c_uint64), ("n_superkmers", ctypes.c_uint64),
+        ("n_sorted_keys", ctypes.c_uint64), ("n_distinct", ctypes.c_uint64),
+        ("n_out", ctypes.c_uint64), ("max_bin_kmers", ctypes.c_uint64),
+        ("bin_bytes", ctypes.c_uint64), ("x_used", ctypes.c_uint32), ("m_used", ctypes.c_uint32),
+        ("n_tiles", ctypes.c_uint32), ("n_big_tiles", ctypes.c_uint32),
+        ("ms_distribute", ctypes.c_float), ("ms_sort", ctypes.c_float),
+        ("ms_order", ctypes.c_float), ("ms_total", ctypes.c_float),
+        ("ms_stage", ctypes.c_float * 12), ("n_launches", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["ms_stage"] = {STAGES[i]: float(self.ms_stage[i]) for i in range(len(STAGES))}
+        return d
+
+
+# kmc_stats.ms_stage indices (KMC_STAGE_* in include/kmc.h)
+STAGES = ["pack", "signature", "bin_scatter", "bin_map", "kx_count", "plan", "kx_scatter",
+          "tile_sort", "big_sort", "order", "other"]
+
+
+class KmcError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_vp = ctypes.c_void_p
+
+# (name, restype, argtypes) of every exported symbol of include/kmc.h
+SIGNATURES = [
+    ("kmc_default_params", None, [ctypes.POINTER(kmc_params)]),
+    ("kmc_open", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(kmc_params)]),
+    ("kmc_add_reads", ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_uint64]),
+    ("kmc_add_reads_device", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint64]),
+    ("kmc_count", ctypes.c_int, [_vp]),
+    ("kmc_result_size", ctypes.c_int, [_vp, _u64p]),
+    ("kmc_result", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_uint64, _u64p]),
+    ("kmc_result_device", ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _u64p]),
+    ("kmc_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_stats)]),
+    ("kmc_reset", ctypes.c_int, [_vp]),
+    ("kmc_close", None, [_vp]),
+    ("kmc_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("kmc_set_bin_map", ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
+    ("kmc_get_bin_map", ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
+    ("kmc_debug_superkmers", ctypes.c_int, [_vp, _u64p, _u32p, _u32p, _u32p, ctypes.c_uint64, _u64p]),
+    ("kmc_debug_bin_keys", ctypes.c_int, [_vp, ctypes.c_uint32, _u64p, ctypes.c_uint64, _u64p, _u32p]),
+]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libkmc.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libkmc.so not built ({path}); run __graft_entry__.build()")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return load().kmc_strerror(code).decode()
+
+
+def _check(rc, what):
+    if rc != KMC_OK:
+        raise KmcError(rc, what)
+
+
+def _ptr(a, ct=ctypes.c_uint8):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+# ----------------------------------------------------------- C-ABI mirror
+
+def kmc_default_params() -> kmc_params:
+    p = kmc_params()
+    load().kmc_default_params(ctypes.byref(p))
+    return p
+
+
+def kmc_open(p: kmc_params) -> int:
+    h = _vp()
+    _check(load().kmc_open(ctypes.byref(h), ctypes.byref(p)), "kmc_open")
+    return h.value
+
+
+def kmc_add_reads(h, bases: np.ndarray, offsets: np.ndarray):
+    bases = np.ascontiguousarray(bases, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    _check(load().kmc_add_reads(h, bases.ctypes.data if bases.size else None, _ptr(offsets, ctypes.c_uint64),
+                                offsets.size - 1), "kmc_add_reads")
+
+
+def kmc_add_reads_ptr(h, bases_ptr: int, offsets_ptr: int, n_reads: int):
+    """kmc_add_reads on raw host pointers (e.g. pinned torch tensors)."""
+    _check(load().kmc_add_reads(h, bases_ptr, ctypes.cast(offsets_ptr, _u64p), n_reads), "kmc_add_reads")
+
+
+def kmc_add_reads_device(h, d_bases_ptr: int, d_offsets_ptr: int, n_reads: int, n_bases: int):
+    _check(load().kmc_add_reads_device(h, d_bases_ptr, d_offsets_ptr, n_reads, n_bases),
+           "kmc_add_reads_device")
+
+
+def kmc_count(h):
+    _check(load().kmc_count(h), "kmc_count")
+
+
+def kmc_result_size(h) -> int:
+    n = ctypes.c_uint64()
+    _check(load().kmc_result_size(h, ctypes.byref(n)), "kmc_result_size")
+    return n.value
+
+
+def kmc_result(h, k: int):
+    n = kmc_result_size(h)
+    words = (k + 31) // 32
+    kms = np.empty((n, words), dtype=np.uint64)
+    cnt = np.empty(n, dtype=np.uint32)
+    nout = ctypes.c_uint64()
+    _check(load().kmc_result(h, kms.ctypes.data if n else None, cnt.ctypes.data if n else None, n,
+                             ctypes.byref(nout)), "kmc_result")
+    return kms, cnt
+
+
+def kmc_result_device(h):
+    dk, dc, n = _vp(), _vp(), ctypes.c_uint64()
+    _check(load().kmc_result_device(h, ctypes.byref(dk), ctypes.byref(dc), ctypes.byref(n)),
+           "kmc_result_device")
+    return dk.value, dc.value, n.value
+
+
+def kmc_stats_get(h) -> dict:
+    s = kmc_stats()
+    _check(load().kmc_stats_get(h, ctypes.byref(s)), "kmc_stats_get")
+    return s.as_dict()
+
+
+def kmc_reset(h):
+    _check(load().kmc_reset(h), "kmc_reset")
+
+
+def kmc_close(h):
+    if h:
+        load().kmc_close(h)
+
+
+def kmc_set_bin_map(h, mp: np.ndarray):
+    mp = np.ascontiguousarray(mp, dtype=np.uint32)
+    _check(load().kmc_set_bin_map(h, _ptr(mp, ctypes.c_uint32), mp.size), "kmc_set_bin_map")
+
+
+def kmc_get_bin_map(h, n_entries: int) -> np.ndarray:
+    mp = np.empty(n_entries, dtype=np.uint32)
+    _check(load().kmc_get_bin_map(h, _ptr(mp, ctypes.c_uint32), n_entries), "kmc_get_bin_map")
+    return mp
+
+
+def kmc_debug_superkmers(h):
+    n = ctypes.c_uint64()
+    rc = load().kmc_debug_superkmers(h, None, None, None, None, 0, ctypes.byref(n))
+    if rc not in (KMC_OK, KMC_ETRUNC):
+        _check(rc, "kmc_debug_superkmers")
+    cap = n.value
+    rd = np.empty(max(cap, 1), np.uint64)
+    ps = np.empty(max(cap, 1), np.uint32)
+    nk = np.empty(max(cap, 1), np.uint32)
+    sg = np.empty(max(cap, 1), np.uint32)
+    _check(load().kmc_debug_superkmers(h, _ptr(rd, ctypes.c_uint64), _ptr(ps, ctypes.c_uint32),
+                                       _ptr(nk, ctypes.c_uint32), _ptr(sg, ctypes.c_uint32), cap,
+                                       ctypes.byref(n)), "kmc_debug_superkmers")
+    return rd[:cap], ps[:cap], nk[:cap], sg[:cap]
+
+
+def kmc_debug_bin_keys(h, b: int):
+    n = ctypes.c_uint64()
+    w = ctypes.c_uint32()
+    rc = load().kmc_debug_bin_keys(h, b, None, 0, ctypes.byref(n), ctypes.byref(w))
+    if rc not in (KMC_OK, KMC_ETRUNC):
+        _check(rc, "kmc_debug_bin_keys")
+    keys = np.empty((max(n.value, 1), max(w.value, 1)), np.uint64)
+    _check(load().kmc_debug_bin_keys(h, b, _ptr(keys, ctypes.c_uint64), n.value, ctypes.byref(n),
+                                     ctypes.byref(w)), "kmc_debug_bin_keys")
+    return keys[:n.value]
+
+
+# ----------------------------------------------------------- convenience
+
+def make_params(k, m=7, n_bins=512, x=KMC_AUTO, cutoff_min=2, cutoff_max=10**9, device=0,
+                stream=None, debug_flags=0, piece_bytes=0) -> kmc_params:
+    p = kmc_default_params()
+    p.k, p.m, p.n_bins = k, m, n_bins
+    p.x = KMC_AUTO if x is None else x
+    p.cutoff_min, p.cutoff_max = cutoff_min, cutoff_max
+    p.device = device
+    p.cuda_stream = stream
+    p.debug_flags = debug_flags
+    p.piece_bytes = piece_bytes
+    return p
+
+
+class Counter:
+    """One counting job: open -> add reads -> count -> result -> close."""
+
+    def __init__(self, k, **kw):
+        self.k = k
+        self.params = make_params(k, **kw)
+        self.h = kmc_open(self.params)
+
+    def add(self, bases, offsets):
+        kmc_add_reads(self.h, bases, offsets)
+        return self
+
+    def add_device(self, d_bases, d_offsets):
+        """Reads already on the device (torch CUDA tensors: uint8 bases, int64 offsets)."""
+        kmc_add_reads_device(self.h, d_bases.data_ptr(), d_offsets.data_ptr(),
+                             d_offsets.numel() - 1, d_bases.numel())
+        return self
+
+    def count(self):
+        kmc_count(self.h)
+        return self
+
+    def result(self):
+        return kmc_result(self.h, self.k)
+
+    def size(self):
+        return kmc_result_size(self.h)
+
+    def stats(self):
+        return kmc_stats_get(self.h)
+
+    def close(self):
+        kmc_close(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def count(bases, offsets, k, **kw):
+    """Counts canonical k-mers of host reads; returns (kmers uint64[n, words], counts uint32[n])."""
+    with Counter(k, **kw) as c:
+        return c.add(bases, offsets).count().result()

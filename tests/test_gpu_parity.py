@@ -1,0 +1,230 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every comparison is element by element and exact: the result is a list of
+integers (canonical k-mers and counts), so the bar is bit-exact equality.
+Inputs are seeded and synthetic; the oracle never sees anything produced by
+the CUDA path.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import strings as S
+from paper_1407_1507_gb300 import kmc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_count(bases, offsets, k, **kw):
+    return kmc.count(bases, offsets, k, **kw)
+
+
+def oracle_count(bases, offsets, k, ci=2, cx=10**9):
+    return oracle.count(bases, offsets, k, ci, cx, threads=8)
+
+
+def assert_same(got, want):
+    gk, gc = got
+    wk, wc = want
+    assert gk.shape == wk.shape, (gk.shape, wk.shape)
+    assert np.array_equal(gk, wk)
+    assert np.array_equal(gc, wc)
+
+
+def rand_reads(rng, n, lo, hi, p_n=0.0, alphabet="ACGT"):
+    out = []
+    for _ in range(n):
+        L = rng.randint(lo, hi)
+        out.append("".join(rng.choice(alphabet) if rng.random() >= p_n else "N" for _ in range(L)))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_small_inputs(seed):
+    rng = random.Random(1000 + seed)
+    k = rng.choice([1, 2, 4, 7, 12, 15, 21, 27, 28, 31, 32, 33, 40, 55, 63, 64])
+    m = rng.choice([3, 4, 5, 7, 9, 11])
+    B = rng.choice([1, 3, 64, 512, 2048])
+    reads = rand_reads(rng, rng.randint(1, 300), 0, rng.choice([40, 150, 400]),
+                       p_n=rng.choice([0.0, 0.01, 0.05]), alphabet=rng.choice(["ACGT", "ACGT", "AC"]))
+    ci = rng.choice([1, 2])
+    b, o = oracle.as_reads(reads)
+    assert_same(gpu_count(b, o, k, m=m, n_bins=B, cutoff_min=ci), oracle_count(b, o, k, ci))
+
+
+def test_tiny_workload_full_size():
+    w = synth.tiny()
+    got = gpu_count(w.bases, w.offsets, w.k, m=w.m, n_bins=w.n_bins)
+    want = oracle_count(w.bases, w.offsets, w.k)
+    assert want[0].shape[0] > 100_000
+    assert_same(got, want)
+
+
+@pytest.mark.parametrize("k", [21, 28, 31, 32, 55, 64])
+def test_mid_workload_scaled(k):
+    w = synth.mid(scale=0.004)
+    got = gpu_count(w.bases, w.offsets, k, m=w.m, n_bins=w.n_bins)
+    assert_same(got, oracle_count(w.bases, w.offsets, k))
+
+
+def test_large_workload_scaled_m9():
+    w = synth.large(k=28, scale=0.002)
+    for k in (28, 55):
+        got = gpu_count(w.bases, w.offsets, k, m=9, n_bins=2048)
+        assert_same(got, oracle_count(w.bases, w.offsets, k))
+
+
+def test_result_independent_of_bins_and_signature_length():
+    w = synth.mid(scale=0.002)
+    want = oracle_count(w.bases, w.offsets, 28)
+    for B in (1, 64, 512, 2048):
+        assert_same(gpu_count(w.bases, w.offsets, 28, m=7, n_bins=B), want)
+    for m in (3, 5, 9, 11):
+        assert_same(gpu_count(w.bases, w.offsets, 28, m=m, n_bins=256), want)
+
+
+def test_cutoffs_inclusive_and_ci1():
+    w = synth.tiny(scale=0.02)
+    for ci, cx in [(1, 2**32 - 1), (2, 3), (3, 3), (5, 10**9), (1, 1)]:
+        got = gpu_count(w.bases, w.offsets, 25, m=7, n_bins=16, cutoff_min=ci, cutoff_max=cx)
+        assert_same(got, oracle_count(w.bases, w.offsets, 25, ci, cx))
+
+
+def test_total_count_is_number_of_positions():
+    w = synth.mid(scale=0.002)
+    with kmc.Counter(28, m=7, n_bins=64, cutoff_min=1, cutoff_max=2**32 - 1) as c:
+        kms, cnt = c.add(w.bases, w.offsets).count().result()
+        st = c.stats()
+    _, _, npos = oracle.count(w.bases, w.offsets, 28, 1, 2**32 - 1, threads=8, return_npos=True)
+    assert int(cnt.astype(np.uint64).sum()) == npos == st["n_kmer_positions"]
+
+
+def test_heavy_repeats_take_the_big_tile_path():
+    # one read repeated 30k times: each of its k-mers has 30k copies, far above a tile
+    rng = random.Random(5)
+    r = "".join(rng.choice("ACGT") for _ in range(60))
+    reads = [r] * 30000 + ["A" * 80] * 2000 + rand_reads(rng, 500, 20, 120)
+    b, o = oracle.as_reads(reads)
+    with kmc.Counter(21, m=7, n_bins=8) as c:
+        got = c.add(b, o).count().result()
+        st = c.stats()
+    assert st["n_big_tiles"] > 0
+    assert_same(got, oracle_count(b, o, 21))
+
+
+def test_poly_a_and_low_complexity():
+    reads = ["A" * 200, "T" * 150, "AC" * 80, "ACGT" * 40, "AAAAAAAAAAAAAAAAAAAAAAAAAAAAAC" * 3]
+    b, o = oracle.as_reads(reads * 3)
+    for k in (5, 28, 33):
+        assert_same(gpu_count(b, o, k, m=7, n_bins=4, cutoff_min=1), oracle_count(b, o, k, 1))
+
+
+def test_empty_and_short_inputs():
+    for reads in ([], [""], ["ACG"], ["", "", "ACGTACGTAC"], ["NNNN", "ACGTNACGT"]):
+        b, o = oracle.as_reads(reads)
+        got = gpu_count(b, o, 5, m=3, n_bins=4, cutoff_min=1)
+        assert_same(got, oracle_count(b, o, 5, 1))
+
+
+def test_multiple_add_calls_append():
+    w = synth.tiny(scale=0.01)
+    n = w.n_reads
+    h1 = n // 3
+    with kmc.Counter(28, m=7, n_bins=64) as c:
+        c.add(w.bases[: int(w.offsets[h1])], w.offsets[: h1 + 1])
+        o2 = w.offsets[h1:] - w.offsets[h1]
+        c.add(w.bases[int(w.offsets[h1]):], o2)
+        got = c.count().result()
+    assert_same(got, oracle_count(w.bases, w.offsets, 28))
+
+
+def test_recount_is_identical():
+    w = synth.tiny(scale=0.01)
+    with kmc.Counter(28, m=7, n_bins=64) as c:
+        c.add(w.bases, w.offsets)
+        a = c.count().result()
+        b = c.count().result()
+    assert_same(a, b)
+
+
+def test_device_input_equals_host_input():
+    torch = pytest.importorskip("torch")
+    w = synth.mid(scale=0.002)
+    want = oracle_count(w.bases, w.offsets, 28)
+    db = torch.from_numpy(w.bases).cuda()
+    do = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    # an unaligned start exercises the stream alignment
+    with kmc.Counter(28, m=7, n_bins=512, stream=torch.cuda.current_stream().cuda_stream) as c:
+        got = c.add_device(db, do).count().result()
+    assert_same(got, want)
+    pad = torch.zeros(w.bases.size + 3, dtype=torch.uint8, device="cuda")
+    pad[3:] = db
+    with kmc.Counter(28, m=7, n_bins=512) as c:
+        kmc.kmc_add_reads_device(c.h, pad.data_ptr() + 3, do.data_ptr(), w.n_reads, w.bases.size)
+        got = c.count().result()
+    assert_same(got, want)
+
+
+def test_superkmers_match_oracle_split():
+    w = synth.mid(scale=0.0005)
+    k, m = 28, 7
+    with kmc.Counter(k, m=m, n_bins=64, debug_flags=kmc.KMC_DEBUG_KEEP_SUPERKMERS) as c:
+        c.add(w.bases, w.offsets)
+        rd, ps, nk, sg = kmc.kmc_debug_superkmers(c.h)
+    got = sorted(zip(rd.tolist(), ps.tolist(), nk.tolist(), sg.tolist()))
+    want = []
+    for r in range(w.n_reads):
+        a, e = int(w.offsets[r]), int(w.offsets[r + 1])
+        for st, n, g in oracle.superkmers(bytes(w.bases[a:e]), k, m, cut_every=128):
+            want.append((r, st, n, g))
+    assert got == sorted(want)
+
+
+def test_bin_map_matches_oracle_reading():
+    w = synth.mid(scale=0.001)
+    k, m, B = 28, 7, 64
+    with kmc.Counter(k, m=m, n_bins=B) as c:
+        c.add(w.bases, w.offsets)
+        got = kmc.kmc_get_bin_map(c.h, 4 ** m + 1)
+    ps = oracle.position_sigs(w.bases, w.offsets, k, m)
+    ps = ps[ps != oracle.NO_KMER]
+    weights = np.bincount(ps, minlength=4 ** m + 1).astype(np.uint64)
+    assert np.array_equal(got, oracle.bin_map(weights, B))
+
+
+def test_user_bin_map_does_not_change_result():
+    w = synth.tiny(scale=0.01)
+    want = oracle_count(w.bases, w.offsets, 28)
+    mp = np.random.default_rng(3).integers(0, 5, size=4 ** 7 + 1).astype(np.uint32)
+    with kmc.Counter(28, m=7, n_bins=5) as c:
+        kmc.kmc_set_bin_map(c.h, mp)
+        got = c.add(w.bases, w.offsets).count().result()
+    assert_same(got, want)
+
+
+def test_errors_are_reported():
+    b, o = oracle.as_reads(["ACGTACGTAC", "ACGT"])
+    with kmc.Counter(5, m=3, n_bins=2) as c:
+        with pytest.raises(kmc.KmcError) as e:
+            kmc.kmc_result_size(c.h)
+        assert e.value.code == kmc.KMC_ESTATE
+        bad = o.copy()
+        bad[1], bad[2] = bad[2], bad[1]
+        with pytest.raises(kmc.KmcError) as e:
+            c.add(b, bad)
+        assert e.value.code == kmc.KMC_EINPUT
+
+
+@pytest.mark.parametrize("piece_bytes", [1 << 12, 100_000, 1 << 20])
+def test_many_pieces_host_and_device(piece_bytes):
+    torch = pytest.importorskip("torch")
+    w = synth.mid(scale=0.002)
+    want = oracle_count(w.bases, w.offsets, 28)
+    got = gpu_count(w.bases, w.offsets, 28, m=7, n_bins=128, piece_bytes=piece_bytes)
+    assert_same(got, want)
+    db = torch.from_numpy(w.bases).cuda()
+    do = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
+    with kmc.Counter(28, m=7, n_bins=128, piece_bytes=piece_bytes) as c:
+        assert_same(c.add_device(db, do).count().result(), want)
