@@ -219,11 +219,14 @@ def run_ours(args, rank, local_rank, world):
     alg = stage_bytes(st0, k)
     dom = max((s for s in alg), key=lambda s: per.get(s, 0.0))
     stages = {}
-    for s, b in alg.items():
-        if per.get(s, 0) > 0:
-            gbs = b / (per[s] / 1e3) / 1e9
-            stages[s] = {"ms": round(per[s], 4), "alg_bytes": int(b), "gbs": round(gbs, 1),
-                         "frac": round(gbs / peak, 4)}
+    for s, t in per.items():
+        if t <= 0:
+            continue
+        stages[s] = {"ms": round(t, 4)}
+        if s in alg:
+            gbs = alg[s] / (t / 1e3) / 1e9
+            stages[s].update({"alg_bytes": int(alg[s]), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
+    stages["sum_ms"] = round(sum(per.values()), 3)
     achieved = stages[dom]["gbs"]
     roofline = {"bound": "hbm", "kernel_stage": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,

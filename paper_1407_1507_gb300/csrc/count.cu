@@ -13,8 +13,7 @@ namespace kmc {
 namespace {
 
 constexpr int KX_THREADS = 256;
-constexpr int KX_RECORDS_PER_CHUNK = 1024;
-constexpr int KX_MAX_D = 12;
+constexpr int KX_RECORDS_PER_CHUNK = 512;
 constexpr int CNT_THREADS = 256;
 constexpr int CNT_IPT64 = 32;   // tile = 8192 64-bit keys
 constexpr int CNT_IPT128 = 16;  // tile = 4096 128-bit keys
@@ -81,18 +80,6 @@ __device__ __forceinline__ void locate(const RecBatch &b, uint32_t it, uint32_t 
   *j = lo + lane - ks;
 }
 
-// Cheap digit of the canonical k-mer for x = 0: the top D bits of
-// min(kmer, revcomp(kmer)) equal min(first D/2 symbols, revcomp of the last
-// D/2 symbols), since the top bits decide the minimum unless they tie.
-__device__ __forceinline__ uint32_t kmer_digit(const uint64_t *wds, uint32_t j, int k, int D) {
-  if (D == 0) return 0;
-  const int h = D / 2;
-  uint32_t f = (uint32_t)get_bits(wds, 2ull * j, D);
-  uint32_t l = (uint32_t)get_bits(wds, 2ull * (j + k - h), D);
-  uint32_t r = revcomp32(l, h);
-  return f < r ? f : r;
-}
-
 template <typename K>
 __device__ __forceinline__ K canonical_kmer(const uint64_t *wds, uint32_t j, int k);
 template <>
@@ -108,74 +95,29 @@ __device__ __forceinline__ u128 canonical_kmer<u128>(const uint64_t *wds, uint32
   return f < r ? f : r;
 }
 
-// a4, count pass (x = 0): per-bin histogram of the top D bits of every
-// canonical k-mer of the chunk's super k-mers.
-__global__ void __launch_bounds__(KX_THREADS)
-kx0_count_kernel(const Chunk *__restrict__ chunks, const PieceDesc *__restrict__ pieces, int k,
-                 int D, uint32_t *__restrict__ hist) {
-  __shared__ uint32_t h[1 << KX_MAX_D];
-  const uint32_t ND = 1u << D;
-  const Chunk c = chunks[blockIdx.x];
-  const PieceDesc pd = pieces[c.piece];
-  for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS) h[i] = 0;
-  __syncthreads();
-  const unsigned w = threadIdx.x >> 5, lane = lane_id();
-  const uint64_t r_end = c.r0 + c.n_rec;
-  for (uint64_t r = c.r0 + 32ull * w; r < r_end; r += 32ull * (KX_THREADS / 32)) {
-    RecBatch b = load_batch(pd.index, r, r_end);
-    for (uint32_t it = 0; 32 * it < b.total; ++it) {
-      uint32_t rec, j;
-      locate(b, it, &rec, &j);
-      const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
-      const bool ok = 32 * it + lane < b.total;
-      const uint32_t d = ok ? kmer_digit(pd.words + woff, j, k, D) : 0xFFFFFFFFu;
-      const unsigned peers = __match_any_sync(FULL, d);
-      if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
-    }
-  }
-  __syncthreads();
-  uint32_t *hb = hist + (uint64_t)c.bin * ND;
-  for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS)
-    if (h[i]) atomicAdd(&hb[i], h[i]);
-}
-
-// a4, scatter pass (x = 0): canonical k-mers written into their (bin, digit)
-// buckets.  Sweep 1 counts the chunk's digits, one global atomic per digit
-// reserves space, sweep 2 computes the keys and writes them.
+// Shared arguments of the key-building kernels.
 template <typename K>
-__global__ void __launch_bounds__(KX_THREADS)
-kx0_scatter_kernel(const Chunk *__restrict__ chunks, const PieceDesc *__restrict__ pieces, int k,
-                   int D, const uint64_t *__restrict__ bucket_base, uint32_t *__restrict__ cursor,
-                   K *__restrict__ keys, uint64_t n_keys, uint32_t *err) {
-  __shared__ uint32_t h[1 << KX_MAX_D];
-  __shared__ uint64_t gb[1 << KX_MAX_D];
-  const uint32_t ND = 1u << D;
-  const Chunk c = chunks[blockIdx.x];
-  const PieceDesc pd = pieces[c.piece];
-  for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS) h[i] = 0;
-  __syncthreads();
+struct KxArgs {
+  const Chunk *chunks;
+  const PieceDesc *pieces;
+  int k;
+  int key_bits;
+  const uint32_t *group_base;  // first bucket of each bin
+  const uint8_t *group_D;      // digit bits of each bin
+  Mixer<K> mixer;
+};
+
+constexpr int KX_SMEM_D = 12;            // digits aggregated in shared memory up to 2^12
+constexpr int KX_STASH = 1024;           // keys stashed per warp between the two sweeps
+
+// Visits the k-mers of a chunk: warp w takes record batches w, w+8, ...;
+// f(lane_ok, key) is called once per 32-k-mer step with the canonical,
+// mixed key of this lane's k-mer (all lanes call f).
+template <typename K, typename F>
+__device__ __forceinline__ void for_chunk_keys(const KxArgs<K> &a, const Chunk &c, F f) {
+  const PieceDesc pd = a.pieces[c.piece];
   const unsigned w = threadIdx.x >> 5, lane = lane_id();
   const uint64_t r_end = c.r0 + c.n_rec;
-  for (uint64_t r = c.r0 + 32ull * w; r < r_end; r += 32ull * (KX_THREADS / 32)) {
-    RecBatch b = load_batch(pd.index, r, r_end);
-    for (uint32_t it = 0; 32 * it < b.total; ++it) {
-      uint32_t rec, j;
-      locate(b, it, &rec, &j);
-      const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
-      const bool ok = 32 * it + lane < b.total;
-      const uint32_t d = ok ? kmer_digit(pd.words + woff, j, k, D) : 0xFFFFFFFFu;
-      const unsigned peers = __match_any_sync(FULL, d);
-      if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
-    }
-  }
-  __syncthreads();
-  const uint64_t bb = (uint64_t)c.bin * ND;
-  for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS) {
-    if (h[i]) gb[i] = bucket_base[bb + i] + atomicAdd(&cursor[bb + i], h[i]);
-    h[i] = 0;
-  }
-  __syncthreads();
-  const int key_bits = 2 * k;
   for (uint64_t r = c.r0 + 32ull * w; r < r_end; r += 32ull * (KX_THREADS / 32)) {
     RecBatch b = load_batch(pd.index, r, r_end);
     for (uint32_t it = 0; 32 * it < b.total; ++it) {
@@ -184,18 +126,116 @@ kx0_scatter_kernel(const Chunk *__restrict__ chunks, const PieceDesc *__restrict
       const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
       const bool ok = 32 * it + lane < b.total;
       K key = K(0);
-      uint32_t d = 0xFFFFFFFFu;
-      if (ok) {
-        key = canonical_kmer<K>(pd.words + woff, j, k);
-        d = top_digit<K>(key, key_bits, D);
+      if (ok) key = a.mixer.mix(canonical_kmer<K>(pd.words + woff, j, a.k));
+      f(ok, key);
+    }
+  }
+}
+
+// a4, count pass (x = 0): per-bin histogram of the top D bits of every mixed
+// canonical k-mer of the chunk's super k-mers.
+template <typename K>
+__global__ void __launch_bounds__(KX_THREADS)
+kx0_count_kernel(KxArgs<K> a, uint32_t *__restrict__ hist) {
+  __shared__ uint32_t h[1 << KX_SMEM_D];
+  const Chunk c = a.chunks[blockIdx.x];
+  const int D = a.group_D[c.bin];
+  const uint32_t ND = 1u << D;
+  uint32_t *hb = hist + a.group_base[c.bin];
+  const bool in_smem = D <= KX_SMEM_D;
+  if (in_smem) {
+    for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS) h[i] = 0;
+    __syncthreads();
+  }
+  const unsigned lane = lane_id();
+  for_chunk_keys<K>(a, c, [&](bool ok, K key) {
+    const uint32_t d = ok ? top_digit<K>(key, a.key_bits, D) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(FULL, d);
+    if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(in_smem ? &h[d] : &hb[d], (uint32_t)__popc(peers));
+  });
+  if (in_smem) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS)
+      if (h[i]) atomicAdd(&hb[i], h[i]);
+  }
+}
+
+template <typename K>
+struct KxScatterSmem {
+  uint32_t h[1 << KX_SMEM_D];      // chunk count per digit, then running rank
+  uint32_t gb[1 << KX_SMEM_D];     // chunk base per digit, relative to the bin's first key
+  K stash[KX_THREADS / 32][KX_STASH];
+};
+
+// a4, scatter pass (x = 0): mixed canonical k-mers written into their (bin,
+// digit) buckets.  Sweep 1 computes the keys (stashed in shared memory) and
+// counts the chunk's digits; one global atomic per digit reserves space;
+// sweep 2 writes every key at its place.
+template <typename K>
+__global__ void __launch_bounds__(KX_THREADS)
+kx0_scatter_kernel(KxArgs<K> a, const uint64_t *__restrict__ bucket_base,
+                   uint32_t *__restrict__ cursor, K *__restrict__ keys, uint64_t n_keys,
+                   uint32_t *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  KxScatterSmem<K> &s = *reinterpret_cast<KxScatterSmem<K> *>(smem_raw);
+  const Chunk c = a.chunks[blockIdx.x];
+  const int D = a.group_D[c.bin];
+  const uint32_t ND = 1u << D;
+  const uint32_t g0 = a.group_base[c.bin];
+  const uint64_t bin_base = bucket_base[g0];
+  const bool in_smem = D <= KX_SMEM_D;
+  const unsigned w = threadIdx.x >> 5, lane = lane_id();
+  if (in_smem) {
+    for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS) s.h[i] = 0;
+    __syncthreads();
+  }
+  uint32_t n_stashed = 0;  // per warp (uniform inside the warp)
+  for_chunk_keys<K>(a, c, [&](bool ok, K key) {
+    if (n_stashed < KX_STASH) s.stash[w][n_stashed + lane] = key;  // KX_STASH % 32 == 0
+    n_stashed += 32;
+    if (in_smem) {
+      const uint32_t d = ok ? top_digit<K>(key, a.key_bits, D) : 0xFFFFFFFFu;
+      const unsigned peers = __match_any_sync(FULL, d);
+      if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(&s.h[d], (uint32_t)__popc(peers));
+    }
+  });
+  if (in_smem) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < ND; i += KX_THREADS) {
+      if (s.h[i]) s.gb[i] = (uint32_t)(bucket_base[g0 + i] - bin_base) + atomicAdd(&cursor[g0 + i], s.h[i]);
+      s.h[i] = 0;
+    }
+    __syncthreads();
+  }
+  __syncwarp();
+  // sweep 2: keys from the stash (recomputed past its capacity)
+  const PieceDesc pd = a.pieces[c.piece];
+  const uint64_t r_end = c.r0 + c.n_rec;
+  uint32_t idx = 0;
+  for (uint64_t r = c.r0 + 32ull * w; r < r_end; r += 32ull * (KX_THREADS / 32)) {
+    RecBatch b = load_batch(pd.index, r, r_end);
+    for (uint32_t it = 0; 32 * it < b.total; ++it, idx += 32) {
+      const bool ok = 32 * it + lane < b.total;
+      K key;
+      if (idx < KX_STASH) {
+        key = s.stash[w][idx + lane];
+      } else {
+        uint32_t rec, j;
+        locate(b, it, &rec, &j);
+        const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
+        key = ok ? a.mixer.mix(canonical_kmer<K>(pd.words + woff, j, a.k)) : K(0);
       }
+      const uint32_t d = ok ? top_digit<K>(key, a.key_bits, D) : 0xFFFFFFFFu;
       const unsigned peers = __match_any_sync(FULL, d);
       const int leader = __ffs(peers) - 1;
-      uint32_t base = 0;
-      if (ok && (int)lane == leader) base = atomicAdd(&h[d], (uint32_t)__popc(peers));
+      uint64_t base = 0;
+      if (ok && (int)lane == leader) {
+        if (in_smem) base = bin_base + s.gb[d] + atomicAdd(&s.h[d], (uint32_t)__popc(peers));
+        else base = bucket_base[g0 + d] + atomicAdd(&cursor[g0 + d], (uint32_t)__popc(peers));
+      }
       base = __shfl_sync(FULL, base, leader);
       if (ok) {
-        const uint64_t p = gb[d] + base + __popc(peers & lanemask_lt());
+        const uint64_t p = base + __popc(peers & lanemask_lt());
         if (p < n_keys) keys[p] = key; else atomicOr(err, ERR_CAPACITY);
       }
     }
@@ -216,9 +256,28 @@ inline unsigned grid_for(uint64_t n, int threads, int cap = 1 << 20) {
   return (unsigned)std::min<uint64_t>(g, (uint64_t)cap);
 }
 
+// Host-side constants of the bijective key mix for key_bits-bit keys.
+template <typename K>
+Mixer<K> make_mixer(int key_bits) {
+  Mixer<K> m;
+  m.bits = key_bits;
+  m.mask = key_bits >= (int)(8 * sizeof(K)) ? ~K(0) : ((K(1) << key_bits) - 1);
+  K c = (K)0x9E3779B97F4A7C15ull;
+  if (sizeof(K) > 8) c = (c << 64) | (K)0xD1B54A32D192ED03ull;
+  c |= 1;
+  K inv = c;  // Newton iteration for the inverse modulo 2^(8 sizeof K)
+  for (int i = 0; i < 7; ++i) inv *= K(2) - c * inv;
+  m.c = c & m.mask;
+  m.cinv = inv & m.mask;
+  m.s1 = (key_bits + 1) / 2;
+  m.s2 = key_bits / 3 + 1;
+  m.on = true;
+  return m;
+}
+
 template <typename K, int IPT>
 int count_tiles(Handle &h, SortScratch &ss, const TilePlan &plan, uint64_t n_keys, K *keys,
-                uint64_t *n_sv_out) {
+                const Mixer<K> &mixer, uint64_t *n_sv_out) {
   using SM = TileCountSmem<K, CNT_THREADS, IPT>;
   using BSM = BigSmem<K, NoVal, CNT_THREADS, BIG_IPT>;
   constexpr int TILE = CNT_THREADS * IPT;
@@ -240,11 +299,7 @@ int count_tiles(Handle &h, SortScratch &ss, const TilePlan &plan, uint64_t n_key
   out.ci = ci;
   out.cx = h.p.cutoff_max;
   out.n_distinct = c64 + 1;
-  K *sorted_out = nullptr;
-  if (h.p.debug_flags & KMC_DEBUG_KEEP_KEYS) {
-    if (dev_ensure(ss.sorted_keys, (n_keys + 1) * sizeof(K), h.st)) return KMC_ENOMEM;
-    sorted_out = as<K>(ss.sorted_keys);
-  }
+  out.mixer = mixer;
   static bool attr = false;
   if (!attr) {
     KMC_CUDA_TRY(cudaFuncSetAttribute(tile_count_kernel<K, CNT_THREADS, IPT>,
@@ -258,10 +313,10 @@ int count_tiles(Handle &h, SortScratch &ss, const TilePlan &plan, uint64_t n_key
       &occ, tile_count_kernel<K, CNT_THREADS, IPT>, CNT_THREADS, sizeof(SM)));
   const unsigned grid = (unsigned)std::max(1, occ) * (unsigned)h.sm_count;
   {
-  StageScope sc(h, KMC_STAGE_TILE_SORT);
-  tile_count_kernel<K, CNT_THREADS, IPT><<<grid, CNT_THREADS, sizeof(SM), h.st>>>(
-      keys, plan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
-      as<uint32_t>(h.err), sorted_out); KMC_COUNT_LAUNCH();
+    StageScope sc(h, KMC_STAGE_TILE_SORT);
+    tile_count_kernel<K, CNT_THREADS, IPT><<<grid, CNT_THREADS, sizeof(SM), h.st>>>(
+        keys, plan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
+        as<uint32_t>(h.err), (K *)nullptr); KMC_COUNT_LAUNCH();
   }
   KMC_CUDA_TRY(cudaGetLastError());
   uint32_t nbig = 0;
@@ -277,10 +332,6 @@ int count_tiles(Handle &h, SortScratch &ss, const TilePlan &plan, uint64_t n_key
         keys, plan, as<uint32_t>(ss.big_list), as<K>(ss.big_scratch), c64 + 3, out,
         as<uint32_t>(h.err)); KMC_COUNT_LAUNCH();
     KMC_CUDA_TRY(cudaGetLastError());
-    if (sorted_out) {
-      // big buckets are sorted in place or in scratch; for inspection, re-run
-      // nothing: the debug copy of big tiles is written by copying them now
-    }
   }
   unsigned long long vals[2];
   KMC_CUDA_TRY(cudaMemcpyAsync(vals, c64, 16, cudaMemcpyDeviceToHost, h.st));
@@ -290,37 +341,34 @@ int count_tiles(Handle &h, SortScratch &ss, const TilePlan &plan, uint64_t n_key
   return check_device_error(h);
 }
 
-// Chooses the digit width D (even, <= 12): about TILE/8 keys per bucket of
-// the largest bin.
-int choose_digits(uint64_t max_bin_keys, int key_bits, int tile) {
-  int D = 0;
-  const uint64_t target = (uint64_t)tile / 8;
-  while (D + 2 <= KX_MAX_D && D + 2 <= key_bits && (max_bin_keys >> D) > target) D += 2;
-  return D;
-}
-
-// Tile plan over hist[G*ND] (u32 counts): bucket bases, tile starts.
-int plan_tiles(Handle &h, SortScratch &ss, const uint32_t *hist, uint64_t nbk, uint32_t ND,
-               int tile_cap, DevBuf &base, DevBuf &flags, DevBuf &fscan, DevBuf &tfirst,
-               DevBuf &tmp, uint32_t **n_tiles_dev) {
-  if (dev_ensure(base, (nbk + 1) * 8, h.st) || dev_ensure(flags, nbk * 4 + 4, h.st) ||
-      dev_ensure(fscan, (nbk + 1) * 8, h.st) || dev_ensure(tfirst, nbk * 4 + 8, h.st) ||
-      dev_ensure(tmp, scan_tmp_words(nbk) * 8, h.st))
+// Tile plan over hist[NB] (u32 counts per bucket, grouped by bin).
+int plan_tiles(Handle &h, const uint32_t *hist, uint64_t NB, const uint32_t *group_base,
+               uint32_t n_groups, int tile_cap, DevBuf &base, DevBuf &flags, DevBuf &fscan,
+               DevBuf &tfirst, DevBuf &tmp, uint32_t **n_tiles_dev) {
+  if (dev_ensure(base, (NB + 1) * 8, h.st) || dev_ensure(flags, NB * 4 + 4, h.st) ||
+      dev_ensure(fscan, (NB + 1) * 8, h.st) || dev_ensure(tfirst, NB * 4 + 8, h.st) ||
+      dev_ensure(tmp, scan_tmp_words(NB) * 8, h.st))
     return KMC_ENOMEM;
-  KMC_CUDA_TRY(device_excl_scan_u32(hist, as<uint64_t>(base), nbk, as<uint64_t>(tmp), h.st));
-  plan_flags_kernel<<<grid_for(nbk, 256, 65535), 256, 0, h.st>>>(hist, as<uint64_t>(base), nbk, ND,
-                                                                  (uint32_t)tile_cap,
-                                                                  as<uint32_t>(flags)); KMC_COUNT_LAUNCH();
+  KMC_CUDA_TRY(device_excl_scan_u32(hist, as<uint64_t>(base), NB, as<uint64_t>(tmp), h.st));
+  plan_flags_kernel<<<grid_for(NB, 256, 65535), 256, 0, h.st>>>(
+      hist, as<uint64_t>(base), NB, group_base, n_groups, (uint32_t)tile_cap, as<uint32_t>(flags));
+  KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
-  KMC_CUDA_TRY(device_excl_scan_u32(as<uint32_t>(flags), as<uint64_t>(fscan), nbk, as<uint64_t>(tmp),
-                                    h.st));
-  uint32_t *nt = as<uint32_t>(tfirst) + nbk + 1;
-  plan_emit_kernel<<<grid_for(nbk, 256, 65535), 256, 0, h.st>>>(
-      as<uint32_t>(flags), as<uint64_t>(fscan), nbk, as<uint32_t>(tfirst), nt); KMC_COUNT_LAUNCH();
+  KMC_CUDA_TRY(device_excl_scan_u32(as<uint32_t>(flags), as<uint64_t>(fscan), NB, as<uint64_t>(tmp), h.st));
+  uint32_t *nt = as<uint32_t>(tfirst) + NB + 1;
+  plan_emit_kernel<<<grid_for(NB, 256, 65535), 256, 0, h.st>>>(
+      as<uint32_t>(flags), as<uint64_t>(fscan), NB, as<uint32_t>(tfirst), nt);
+  KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
   *n_tiles_dev = nt;
-  (void)ss;
   return KMC_OK;
+}
+
+// Digit bits of a bin with n keys: about TILE/4 keys per bucket.
+int digits_for(uint64_t n, int key_bits, int tile) {
+  int D = 0;
+  while (D < 20 && D < key_bits && (n >> D) > (uint64_t)tile / 4) ++D;
+  return D;
 }
 
 template <typename K, int IPT>
@@ -335,70 +383,96 @@ int sort_phase_x0(Handle &h) {
   for (uint64_t v : h.bin_kmers) max_bin = std::max(max_bin, v);
   h.stats.max_bin_kmers = max_bin;
   h.stats.n_sorted_keys = n_keys;
-  const int D = choose_digits(max_bin, key_bits, TILE);
-  const uint32_t ND = 1u << D;
-  const uint64_t nbk = (uint64_t)B * ND;
+  // per-bin digit widths and bucket groups
+  std::vector<uint32_t> gbase(B + 1);
+  std::vector<uint8_t> gD(B);
+  uint64_t NB = 0;
+  for (uint32_t b = 0; b < B; ++b) {
+    gD[b] = (uint8_t)digits_for(h.bin_kmers[b], key_bits, TILE);
+    gbase[b] = (uint32_t)NB;
+    NB += 1ull << gD[b];
+  }
+  gbase[B] = (uint32_t)NB;
+  if (NB >= 0xFFFFFFF0ull) return KMC_EINVAL;
   // chunk list: per piece and bin, runs of KX_RECORDS_PER_CHUNK records
   std::vector<Chunk> chunks;
   std::vector<PieceDesc> pds;
   for (size_t p = 0; p < h.pieces.size(); ++p) {
     Piece *pc = h.pieces[p];
     pds.push_back({static_cast<const uint64_t *>(pc->index.p), static_cast<const uint64_t *>(pc->words.p)});
-    std::vector<uint64_t> rb(B + 1);
-    KMC_CUDA_TRY(cudaMemcpyAsync(rb.data(), pc->rec_base.p, (B + 1) * 8, cudaMemcpyDeviceToHost, h.st));
-    KMC_CUDA_TRY(cudaStreamSynchronize(h.st));
+    const std::vector<uint64_t> &rb = pc->rec_base_host;
     for (uint32_t b = 0; b < B; ++b)
       for (uint64_t r = rb[b]; r < rb[b + 1]; r += KX_RECORDS_PER_CHUNK)
         chunks.push_back({r, (uint32_t)std::min<uint64_t>(KX_RECORDS_PER_CHUNK, rb[b + 1] - r),
                           (uint32_t)p, b, 0});
   }
-  if (dev_ensure(ss.counters, 64, h.st) ||
-      dev_ensure(ss.cursor, (chunks.size() + 1) * sizeof(Chunk) + (pds.size() + 1) * sizeof(PieceDesc), h.st) ||
-      dev_ensure(ss.hist, nbk * 4 + 4, h.st))
+  const size_t meta_bytes = (chunks.size() + 1) * sizeof(Chunk) + (pds.size() + 1) * sizeof(PieceDesc) +
+                            (B + 1) * 4 + B + 64;
+  if (dev_ensure(ss.counters, 64, h.st) || dev_ensure(ss.cursor, meta_bytes, h.st) ||
+      dev_ensure(ss.hist, NB * 4 + 4, h.st))
     return KMC_ENOMEM;
+  std::vector<uint8_t> meta(meta_bytes);
   Chunk *d_chunks = as<Chunk>(ss.cursor);
-  PieceDesc *d_pds = reinterpret_cast<PieceDesc *>(d_chunks + chunks.size() + 1);
-  if (!chunks.empty())
-    KMC_CUDA_TRY(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(Chunk),
-                                 cudaMemcpyHostToDevice, h.st));
-  if (!pds.empty())
-    KMC_CUDA_TRY(cudaMemcpyAsync(d_pds, pds.data(), pds.size() * sizeof(PieceDesc),
-                                 cudaMemcpyHostToDevice, h.st));
+  size_t o_pd = (chunks.size() + 1) * sizeof(Chunk);
+  size_t o_gb = o_pd + (pds.size() + 1) * sizeof(PieceDesc);
+  size_t o_gd = o_gb + (B + 1) * 4;
+  memcpy(meta.data(), chunks.data(), chunks.size() * sizeof(Chunk));
+  memcpy(meta.data() + o_pd, pds.data(), pds.size() * sizeof(PieceDesc));
+  memcpy(meta.data() + o_gb, gbase.data(), (B + 1) * 4);
+  memcpy(meta.data() + o_gd, gD.data(), B);
+  KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta.data(), meta_bytes, cudaMemcpyHostToDevice, h.st));
+  KxArgs<K> a;
+  a.chunks = d_chunks;
+  a.pieces = reinterpret_cast<const PieceDesc *>(static_cast<char *>(ss.cursor.p) + o_pd);
+  a.k = k;
+  a.key_bits = key_bits;
+  a.group_base = reinterpret_cast<const uint32_t *>(static_cast<char *>(ss.cursor.p) + o_gb);
+  a.group_D = reinterpret_cast<const uint8_t *>(static_cast<char *>(ss.cursor.p) + o_gd);
+  a.mixer = make_mixer<K>(key_bits);
   uint32_t *hist = as<uint32_t>(ss.hist);
-  KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, nbk * 4, h.st));
+  KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));
   if (!chunks.empty()) {
     StageScope sc(h, KMC_STAGE_KX_COUNT);
-    kx0_count_kernel<<<(unsigned)chunks.size(), KX_THREADS, 0, h.st>>>(d_chunks, d_pds, k, D, hist); KMC_COUNT_LAUNCH();
+    kx0_count_kernel<K><<<(unsigned)chunks.size(), KX_THREADS, 0, h.st>>>(a, hist);
+    KMC_COUNT_LAUNCH();
     KMC_CUDA_TRY(cudaGetLastError());
   }
   uint32_t *n_tiles_dev = nullptr;
   int rc;
   {
     StageScope sc_plan(h, KMC_STAGE_PLAN);
-    rc = plan_tiles(h, ss, hist, nbk, ND, TILE, ss.bucket_base, ss.flags, ss.flag_scan,
+    rc = plan_tiles(h, hist, NB, a.group_base, B, TILE, ss.bucket_base, ss.flags, ss.flag_scan,
                     ss.tile_first, ss.scan_tmp, &n_tiles_dev);
   }
   if (rc) return rc;
   // hist becomes the per-bucket cursor
-  KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, nbk * 4, h.st));
+  KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));
   if (dev_ensure(ss.keys, (n_keys + 1) * sizeof(K), h.st)) return KMC_ENOMEM;
   K *keys = as<K>(ss.keys);
   if (!chunks.empty()) {
+    static bool attr = false;
+    if (!attr) {
+      KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(KxScatterSmem<K>)));
+      attr = true;
+    }
     StageScope sc(h, KMC_STAGE_KX_SCATTER);
-    kx0_scatter_kernel<K><<<(unsigned)chunks.size(), KX_THREADS, 0, h.st>>>(
-        d_chunks, d_pds, k, D, as<uint64_t>(ss.bucket_base), hist, keys, n_keys,
-        as<uint32_t>(h.err)); KMC_COUNT_LAUNCH();
+    kx0_scatter_kernel<K><<<(unsigned)chunks.size(), KX_THREADS, sizeof(KxScatterSmem<K>), h.st>>>(
+        a, as<uint64_t>(ss.bucket_base), hist, keys, n_keys, as<uint32_t>(h.err));
+    KMC_COUNT_LAUNCH();
     KMC_CUDA_TRY(cudaGetLastError());
   }
   TilePlan plan;
   plan.bucket_base = as<uint64_t>(ss.bucket_base);
   plan.tile_first = as<uint32_t>(ss.tile_first);
   plan.n_tiles = n_tiles_dev;
-  plan.ND = ND;
-  plan.D = D;
+  plan.group_base = a.group_base;
+  plan.group_D = a.group_D;
+  plan.n_groups = B;
+  plan.NB = (uint32_t)NB;
   plan.key_bits = key_bits;
   uint64_t n_sv = 0;
-  rc = count_tiles<K, IPT>(h, ss, plan, n_keys, keys, &n_sv);
+  rc = count_tiles<K, IPT>(h, ss, plan, n_keys, keys, a.mixer, &n_sv);
   if (rc) return rc;
   uint32_t nt = 0;
   KMC_CUDA_TRY(cudaMemcpyAsync(&nt, n_tiles_dev, 4, cudaMemcpyDeviceToHost, h.st));
@@ -409,16 +483,15 @@ int sort_phase_x0(Handle &h) {
     return KMC_ENOMEM;
   if (n_sv) {
     StageScope sc(h, KMC_STAGE_ORDER);
+    KMC_CUDA_TRY(cudaMemcpyAsync(h.out_kmers.p, ss.sv_keys.p, n_sv * sizeof(K), cudaMemcpyDeviceToDevice, h.st));
+    KMC_CUDA_TRY(cudaMemcpyAsync(h.out_counts.p, ss.sv_counts.p, n_sv * 4, cudaMemcpyDeviceToDevice, h.st));
     if constexpr (sizeof(K) == 8) {
-      KMC_CUDA_TRY(cudaMemcpyAsync(h.out_kmers.p, ss.sv_keys.p, n_sv * 8, cudaMemcpyDeviceToDevice, h.st));
-      KMC_CUDA_TRY(cudaMemcpyAsync(h.out_counts.p, ss.sv_counts.p, n_sv * 4, cudaMemcpyDeviceToDevice, h.st));
       rc = sort_pairs_u64(h, as<uint64_t>(h.out_kmers), as<uint32_t>(h.out_counts), n_sv, key_bits);
     } else {
-      KMC_CUDA_TRY(cudaMemcpyAsync(h.out_kmers.p, ss.sv_keys.p, n_sv * 16, cudaMemcpyDeviceToDevice, h.st));
-      KMC_CUDA_TRY(cudaMemcpyAsync(h.out_counts.p, ss.sv_counts.p, n_sv * 4, cudaMemcpyDeviceToDevice, h.st));
       rc = sort_pairs_u128(h, as<u128>(h.out_kmers), as<uint32_t>(h.out_counts), n_sv, key_bits);
       if (!rc) {
-        swap_words_kernel<<<grid_for(n_sv, 256, 65535), 256, 0, h.st>>>(as<u128>(h.out_kmers), n_sv); KMC_COUNT_LAUNCH();
+        swap_words_kernel<<<grid_for(n_sv, 256, 65535), 256, 0, h.st>>>(as<u128>(h.out_kmers), n_sv);
+        KMC_COUNT_LAUNCH();
         KMC_CUDA_TRY(cudaGetLastError());
       }
     }

@@ -615,15 +615,18 @@ int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_
                                     as<uint64_t>(ds.scan_tmp), h.st));
   // read back sizes: n_list, total words, per-bin k-mers (host keeps the maximum)
   std::vector<unsigned long long> hk(B);
+  std::vector<uint64_t> rbh(B + 1);
   uint64_t tot[2];
   KMC_CUDA_TRY(cudaMemcpyAsync(&tot[0], cnt, 8, cudaMemcpyDeviceToHost, h.st));
   KMC_CUDA_TRY(cudaMemcpyAsync(&tot[1], word_base + B, 8, cudaMemcpyDeviceToHost, h.st));
   KMC_CUDA_TRY(cudaMemcpyAsync(hk.data(), h_kmers, (size_t)B * 8, cudaMemcpyDeviceToHost, h.st));
+  KMC_CUDA_TRY(cudaMemcpyAsync(rbh.data(), rec_base, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, h.st));
   KMC_CUDA_TRY(cudaStreamSynchronize(h.st));
   rc = check_device_error(h);
   if (rc) return rc;
   const uint64_t n_rec = tot[0], n_words = tot[1];
   Piece *pc = new Piece();
+  pc->rec_base_host = std::move(rbh);
   pc->n_records = n_rec;
   pc->n_words = n_words;
   for (uint32_t b = 0; b < B; ++b) {

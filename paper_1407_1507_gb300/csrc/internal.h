@@ -30,6 +30,7 @@ struct Piece {
   DevBuf index;        // uint64[n_records]
   DevBuf words;        // uint64[n_words + pad]
   DevBuf rec_base;     // uint64[B+1]: first record of each bin
+  std::vector<uint64_t> rec_base_host;
   uint64_t n_records = 0;
   uint64_t n_words = 0;
   uint64_t n_kmers = 0;

@@ -77,14 +77,20 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
       dev_ensure(ss.o_tile_first, (size_t)ND * 4 + 16, h.st) ||
       dev_ensure(ss.o_scan_tmp, scan_tmp_words(ND) * 8, h.st) ||
       dev_ensure(ss.o_big_k, (n + 1) * sizeof(K), h.st) || dev_ensure(ss.o_big_v, (n + 1) * 4, h.st) ||
-      dev_ensure(ss.o_cursor, 64, h.st))
+      dev_ensure(ss.o_cursor, 128, h.st))
     return KMC_ENOMEM;
   uint32_t *hist = as<uint32_t>(ss.o_hist);
   KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)ND * 4, h.st));
   pair_hist_kernel<K><<<grid_for(n, 256, 65535), 256, 0, h.st>>>(keys, n, key_bits, D, hist); KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
   KMC_CUDA_TRY(device_excl_scan_u32(hist, as<uint64_t>(ss.o_base), ND, as<uint64_t>(ss.o_scan_tmp), h.st));
-  plan_flags_kernel<<<grid_for(ND, 256, 65535), 256, 0, h.st>>>(hist, as<uint64_t>(ss.o_base), ND, ND,
+  // one group of ND buckets: group_base = {0, ND}, D
+  uint32_t *grp = as<uint32_t>(ss.o_cursor) + 8;
+  {
+    uint32_t gh[4] = {0u, ND, (uint32_t)D, 0u};
+    KMC_CUDA_TRY(cudaMemcpyAsync(grp, gh, 16, cudaMemcpyHostToDevice, h.st));
+  }
+  plan_flags_kernel<<<grid_for(ND, 256, 65535), 256, 0, h.st>>>(hist, as<uint64_t>(ss.o_base), ND, grp, 1,
                                                                  (uint32_t)TILE, as<uint32_t>(ss.o_flags)); KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
   KMC_CUDA_TRY(device_excl_scan_u32(as<uint32_t>(ss.o_flags), as<uint64_t>(ss.o_flag_scan), ND,
@@ -103,8 +109,10 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
   plan.bucket_base = as<uint64_t>(ss.o_base);
   plan.tile_first = as<uint32_t>(ss.o_tile_first);
   plan.n_tiles = n_tiles;
-  plan.ND = ND;
-  plan.D = D;
+  plan.group_base = grp;
+  plan.group_D = reinterpret_cast<const uint8_t *>(grp + 2);
+  plan.n_groups = 1;
+  plan.NB = ND;
   plan.key_bits = key_bits;
   static bool attr = false;
   if (!attr) {
@@ -115,8 +123,8 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
     attr = true;
   }
   auto *c32 = as<uint32_t>(ss.o_cursor);
-  auto *c64 = reinterpret_cast<unsigned long long *>(c32 + 4);
-  KMC_CUDA_TRY(cudaMemsetAsync(c32, 0, 64, h.st));
+  auto *c64 = reinterpret_cast<unsigned long long *>(c32 + 4);  // c64[0..1] = bytes 16..31
+  KMC_CUDA_TRY(cudaMemsetAsync(c32, 0, 32, h.st));
   const uint32_t big_cap = (uint32_t)std::min<uint64_t>(n / (TILE + 1) + 1, ND);
   if (dev_ensure(ss.o_flags, (size_t)std::max<uint64_t>(ND, big_cap) * 4 + 4, h.st)) return KMC_ENOMEM;
   int occ = 0;

@@ -97,11 +97,12 @@ cudaError_t device_excl_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, 
 // floor(P/half) and holds at most `half` keys, so a tile of several buckets
 // holds fewer than tile_cap keys; a bucket above `half` is a tile alone.
 __global__ void plan_flags_kernel(const uint32_t *cnt, const uint64_t *base, uint64_t nbk,
-                                  uint32_t ND, uint32_t tile_cap, uint32_t *flag) {
+                                  const uint32_t *group_base, uint32_t n_groups,
+                                  uint32_t tile_cap, uint32_t *flag) {
   const uint64_t half = tile_cap / 2;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nbk;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t d = (uint32_t)(i % ND);
+    const uint32_t d = (uint32_t)i - group_base[group_of(group_base, n_groups, (uint32_t)i)];
     uint32_t f = 1;
     if (d != 0) {
       const uint64_t g0 = base[i - d];

@@ -152,33 +152,70 @@ __host__ __device__ __forceinline__ int tile_sort_bits(int key_bits, int D, uint
 }
 
 // ------------------------------------------------------ tile descriptors
-// A tile plan over digit buckets: buckets (group g, digit d) flattened as
-// g*ND + d, bucket_base[i] = first key of bucket i (exclusive scan of the
-// counts, with bucket_base[G*ND] = total).  tile_first[t] = flattened index
-// of the first bucket of tile t; the tile ends where tile t+1 begins (or at
-// the end of its group).
+// A tile plan over digit buckets.  Buckets are grouped (one group per bin;
+// a single group for a plain pair sort); group g has 2^D[g] buckets, the
+// first at flattened index group_base[g].  bucket_base[i] = first key of
+// bucket i (exclusive scan of the counts; bucket_base[NB] = total).
+// tile_first[t] = flattened index of the first bucket of tile t; a tile
+// never crosses a group boundary and ends where tile t+1 begins.
 struct TilePlan {
-  const uint64_t *bucket_base;  // [G*ND + 1]
+  const uint64_t *bucket_base;  // [NB + 1]
   const uint32_t *tile_first;   // [n_tiles]
   const uint32_t *n_tiles;      // device scalar
-  uint32_t ND;                  // digits per group (2^D)
-  int D;
+  const uint32_t *group_base;   // [n_groups + 1]
+  const uint8_t *group_D;       // [n_groups]
+  uint32_t n_groups;
+  uint32_t NB;                  // total buckets
   int key_bits;
 };
 
+// Group holding bucket i (largest g with group_base[g] <= i).
+__device__ __forceinline__ uint32_t group_of(const uint32_t *group_base, uint32_t n_groups,
+                                             uint32_t i) {
+  uint32_t lo = 0, hi = n_groups;  // invariant: group_base[lo] <= i < group_base[hi]
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) / 2;
+    if (group_base[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Key range of tile t and the number of low key bits that vary inside it.
 __device__ __forceinline__ void tile_range(const TilePlan &p, uint32_t t, uint32_t nt,
-                                           uint64_t *start, uint64_t *end, uint32_t *dfirst,
-                                           uint32_t *dlast) {
-  uint32_t i = p.tile_first[t];
-  uint32_t g = i / p.ND;
-  uint32_t inext = (t + 1 < nt) ? p.tile_first[t + 1] : 0xFFFFFFFFu;
-  uint32_t gend = (g + 1) * p.ND;
-  uint32_t j = (inext < gend) ? inext : gend;  // one past the tile's last bucket
+                                           uint64_t *start, uint64_t *end, int *nbits) {
+  const uint32_t i = p.tile_first[t];
+  const uint32_t j = (t + 1 < nt) ? p.tile_first[t + 1] : p.NB;  // one past the last bucket
   *start = p.bucket_base[i];
   *end = p.bucket_base[j];
-  *dfirst = i - g * p.ND;
-  *dlast = j - 1 - g * p.ND;
+  const uint32_t g = group_of(p.group_base, p.n_groups, i);
+  const uint32_t d0 = i - p.group_base[g], d1 = j - 1 - p.group_base[g];
+  *nbits = tile_sort_bits(p.key_bits, p.group_D[g], d0, d1);
 }
+
+// Optional bijective mix of the keys (2^bits values onto themselves): the
+// digit buckets use the top bits of mix(key), which spreads keys evenly
+// whatever their structure; equal keys still share a bucket and a tile.
+// x -> x ^ (x >> s1) -> x * c (mod 2^bits) -> x ^ (x >> s2), c odd.
+template <typename K>
+struct Mixer {
+  K c, cinv, mask;
+  int bits, s1, s2;
+  bool on;
+  __device__ __forceinline__ K mix(K x) const {
+    if (!on) return x;
+    x ^= x >> s1;
+    x = (x * c) & mask;
+    x ^= x >> s2;
+    return x;
+  }
+  __device__ __forceinline__ K unmix(K y) const {
+    if (!on) return y;
+    for (int t = s2; t < bits; t <<= 1) y ^= y >> t;
+    y = (y * cinv) & mask;
+    for (int t = s1; t < bits; t <<= 1) y ^= y >> t;
+    return y;
+  }
+};
 
 // ---------------------------------------------------------------- tile kernels
 
@@ -212,6 +249,7 @@ struct CountOut {
   uint64_t cap;                // capacity of keys/counts
   uint64_t ci, cx;             // inclusive cutoffs (Sect. 2.5)
   unsigned long long *n_distinct;
+  Mixer<K> mixer;              // keys in the tiles are mixed; survivors are not
 };
 
 // Sect. 2.4 "calculates the statistics": run-length count of the sorted keys
@@ -262,7 +300,7 @@ __device__ void tile_rle(const K *s_keys, int n, uint16_t *heads, uint32_t *ws,
         uint32_t h = heads[u];
         uint32_t c = (uint32_t)heads[u + 1] - h;
         if (c >= out.ci && c <= out.cx) {
-          out.keys[base + kb] = s_keys[h];
+          out.keys[base + kb] = out.mixer.unmix(s_keys[h]);
           out.counts[base + kb] = c;
           ++kb;
         }
@@ -300,8 +338,8 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
     const uint32_t t = next_tile(work, &sm.tile);
     if (t >= nt) break;
     uint64_t st, en;
-    uint32_t d0, d1;
-    tile_range(plan, t, nt, &st, &en, &d0, &d1);
+    int nbits;
+    tile_range(plan, t, nt, &st, &en, &nbits);
     const uint64_t n64 = en - st;
     if (n64 == 0) continue;
     if (n64 > (uint64_t)BS::TILE) {
@@ -316,7 +354,7 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
       int e = w * 32 * IPT + i * 32 + lane;
       k[i] = e < n ? keys[st + e] : KeyTraits<K>::max_key();
     }
-    BS::sort(k, v, tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm.bs);
+    BS::sort(k, v, nbits, sm.bs);
     if (sorted_out)
       for (int e = threadIdx.x; e < n; e += THREADS) sorted_out[st + e] = sm.bs.keys[e];
     tile_rle<K, THREADS, IPT>(sm.bs.keys, n, sm.heads, sm.bs.ws, &sm.base, out, err);
@@ -347,8 +385,8 @@ tile_pairs_kernel(K *keys, V *vals, TilePlan plan, uint32_t *work, uint32_t *big
     const uint32_t t = next_tile(work, &sm.tile);
     if (t >= nt) break;
     uint64_t st, en;
-    uint32_t d0, d1;
-    tile_range(plan, t, nt, &st, &en, &d0, &d1);
+    int nbits;
+    tile_range(plan, t, nt, &st, &en, &nbits);
     const uint64_t n64 = en - st;
     if (n64 <= 1) continue;
     if (n64 > (uint64_t)BS::TILE) {
@@ -364,7 +402,7 @@ tile_pairs_kernel(K *keys, V *vals, TilePlan plan, uint32_t *work, uint32_t *big
       k[i] = e < n ? keys[st + e] : KeyTraits<K>::max_key();
       v[i] = e < n ? vals[st + e] : V();
     }
-    BS::sort(k, v, tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm.bs);
+    BS::sort(k, v, nbits, sm.bs);
     for (int e = threadIdx.x; e < n; e += THREADS) {
       keys[st + e] = sm.bs.keys[e];
       vals[st + e] = sm.bs.vals[e];
@@ -495,15 +533,14 @@ big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
   const uint32_t t = big_list[blockIdx.x];
   const uint32_t nt = *plan.n_tiles;
   uint64_t st, en;
-  uint32_t d0, d1;
-  tile_range(plan, t, nt, &st, &en, &d0, &d1);
+  int nbits;
+  tile_range(plan, t, nt, &st, &en, &nbits);
   const uint64_t n = en - st;
   if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
   __syncthreads();
   K *sc = scratch + sm.base;
   const bool in_scratch = big_sort<K, NoVal, THREADS, IPT>(keys + st, (NoVal *)nullptr, sc,
-                                                           (NoVal *)nullptr, n,
-                                                           tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm);
+                                                           (NoVal *)nullptr, n, nbits, sm);
   const K *a = in_scratch ? sc : keys + st;
   // heads: run starts; the run open at the end of a chunk continues in the next
   uint64_t open = 0;  // start of the open run (element 0 always starts one)
@@ -556,7 +593,7 @@ big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
           uint64_t re = r < tot ? c0 + sm.pos[r] : n;
           uint64_t c = re - rs;
           if (c >= out.ci && c <= out.cx && c <= 0xFFFFFFFFull) {
-            out.keys[base + kb] = a[rs];
+            out.keys[base + kb] = out.mixer.unmix(a[rs]);
             out.counts[base + kb] = (uint32_t)c;
             ++kb;
           }
@@ -581,15 +618,14 @@ big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, K *s
   const uint32_t t = big_list[blockIdx.x];
   const uint32_t nt = *plan.n_tiles;
   uint64_t st, en;
-  uint32_t d0, d1;
-  tile_range(plan, t, nt, &st, &en, &d0, &d1);
+  int nbits;
+  tile_range(plan, t, nt, &st, &en, &nbits);
   const uint64_t n = en - st;
   if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
   __syncthreads();
   K *sk = scratch_k + sm.base;
   V *sv = scratch_v + sm.base;
-  if (big_sort<K, V, THREADS, IPT>(keys + st, vals + st, sk, sv, n,
-                                   tile_sort_bits(plan.key_bits, plan.D, d0, d1), sm)) {
+  if (big_sort<K, V, THREADS, IPT>(keys + st, vals + st, sk, sv, n, nbits, sm)) {
     for (uint64_t e = threadIdx.x; e < n; e += THREADS) {
       keys[st + e] = sk[e];
       vals[st + e] = sv[e];
@@ -601,7 +637,8 @@ big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, K *s
 
 // flag[i] = 1 where a tile starts (see plan_tiles in sortlib.cu for the rule).
 __global__ void plan_flags_kernel(const uint32_t *cnt, const uint64_t *base, uint64_t nbk,
-                                  uint32_t ND, uint32_t tile_cap, uint32_t *flag);
+                                  const uint32_t *group_base, uint32_t n_groups,
+                                  uint32_t tile_cap, uint32_t *flag);
 __global__ void plan_emit_kernel(const uint32_t *flag, const uint64_t *flag_scan, uint64_t nbk,
                                  uint32_t *tile_first, uint32_t *n_tiles);
 
