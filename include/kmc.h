@@ -221,6 +221,43 @@ int kmc_debug_superkmers(kmc_handle *h, uint64_t *read_index, uint32_t *pos, uin
 int kmc_debug_bin_keys(kmc_handle *h, uint32_t bin, uint64_t *keys, uint64_t capacity,
                        uint64_t *n_out, uint32_t *words_per_key);
 
+/* ---------------------------------------------------------- no allocation
+ * The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate GPU memory.  Examples: code that runs while a CUDA graph
+ * is being captured (cudaMalloc is not allowed there), a service that owns
+ * a fixed memory budget or hands all device memory to its own allocator,
+ * and latency-sensitive code that cannot afford the device-wide
+ * synchronisation that cudaMalloc / cudaFree may cause.
+ *
+ * kmc_count_small_noalloc counts the canonical k-mers of a small read set
+ * already in device memory and writes the result, sorted ascending by value
+ * and filtered by the inclusive cutoffs, to caller-provided device arrays.
+ * It allocates nothing: its only scratch is a fixed array of
+ * 2 * KMC_NOALLOC_MAX_BASES 64-bit words (16 MiB) compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.
+ *   d_bases / d_offsets: as in kmc_add_reads_device (device memory;
+ *     d_offsets[0] == 0, non-decreasing, d_offsets[n_reads] == n_bases).
+ *   n_bases: at most KMC_NOALLOC_MAX_BASES, else KMC_EINVAL and nothing runs.
+ *   k: 1..32 (one 64-bit word per k-mer), else KMC_EINVAL.
+ *   d_kmers / d_counts: device arrays of `capacity` entries (k-mer value
+ *     right-aligned, count); entries beyond capacity are not written.
+ *   d_n_out: device uint64; receives the number of k-mers in the result
+ *     (possibly above capacity), or UINT64_MAX if the offsets are malformed.
+ * The work is one kernel launched on cuda_stream (NULL = legacy default
+ * stream) of the calling thread's current device; the call returns without
+ * waiting for it.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the scratch array
+ * and it keeps the last call's contents: calls whose kernels may overlap on
+ * the GPU (different streams without ordering) race on it and give wrong
+ * results; order them on one stream. */
+#define KMC_NOALLOC_MAX_BASES (1u << 20)
+int kmc_count_small_noalloc(const char *d_bases, const uint64_t *d_offsets, uint64_t n_reads,
+                            uint64_t n_bases, uint32_t k, uint64_t cutoff_min,
+                            uint64_t cutoff_max, uint64_t *d_kmers, uint32_t *d_counts,
+                            uint64_t capacity, uint64_t *d_n_out, void *cuda_stream);
+
 #define KMC_DEBUG_KEEP_SUPERKMERS 1u
 #define KMC_DEBUG_KEEP_KEYS 2u
 

@@ -93,6 +93,9 @@ SIGNATURES = [
     ("kmc_get_bin_map", ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
     ("kmc_debug_superkmers", ctypes.c_int, [_vp, _u64p, _u32p, _u32p, _u32p, ctypes.c_uint64, _u64p]),
     ("kmc_debug_bin_keys", ctypes.c_int, [_vp, ctypes.c_uint32, _u64p, ctypes.c_uint64, _u64p, _u32p]),
+    ("kmc_count_small_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64,
+                                               _vp, _vp]),
 ]
 
 
@@ -242,6 +245,19 @@ def kmc_debug_bin_keys(h, b: int):
     _check(load().kmc_debug_bin_keys(h, b, _ptr(keys, ctypes.c_uint64), n.value, ctypes.byref(n),
                                      ctypes.byref(w)), "kmc_debug_bin_keys")
     return keys[:n.value]
+
+
+KMC_NOALLOC_MAX_BASES = 1 << 20
+
+
+def kmc_count_small_noalloc(d_bases_ptr, d_offsets_ptr, n_reads, n_bases, k, cutoff_min,
+                            cutoff_max, d_kmers_ptr, d_counts_ptr, capacity, d_n_out_ptr,
+                            stream=None):
+    """Allocation-free count of a small device-resident read set into caller
+    device arrays (see include/kmc.h); asynchronous on `stream`."""
+    _check(load().kmc_count_small_noalloc(d_bases_ptr, d_offsets_ptr, n_reads, n_bases, k,
+                                          cutoff_min, cutoff_max, d_kmers_ptr, d_counts_ptr,
+                                          capacity, d_n_out_ptr, stream), "kmc_count_small_noalloc")
 
 
 # ----------------------------------------------------------- convenience
