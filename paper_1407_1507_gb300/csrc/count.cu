@@ -15,8 +15,8 @@ namespace {
 constexpr int KX_THREADS = 256;
 constexpr int KX_RECORDS_PER_CHUNK = 512;
 constexpr int CNT_THREADS = 256;
-constexpr int CNT_IPT64 = 32;   // tile = 8192 64-bit keys
-constexpr int CNT_IPT128 = 16;  // tile = 4096 128-bit keys
+constexpr int CNT_IPT64 = 16;   // tile = 4096 64-bit keys
+constexpr int CNT_IPT128 = 8;   // tile = 2048 128-bit keys
 constexpr int BIG_IPT = 16;
 
 struct PieceDesc {
@@ -150,8 +150,12 @@ kx0_count_kernel(KxArgs<K> a, uint32_t *__restrict__ hist) {
   const unsigned lane = lane_id();
   for_chunk_keys<K>(a, c, [&](bool ok, K key) {
     const uint32_t d = ok ? top_digit<K>(key, a.key_bits, D) : 0xFFFFFFFFu;
-    const unsigned peers = __match_any_sync(FULL, d);
-    if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(in_smem ? &h[d] : &hb[d], (uint32_t)__popc(peers));
+    if (in_smem) {
+      if (ok) atomicAdd(&h[d], 1u);  // mixed keys: lanes rarely share a digit
+    } else {
+      const unsigned peers = __match_any_sync(FULL, d);
+      if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(&hb[d], (uint32_t)__popc(peers));
+    }
   });
   if (in_smem) {
     __syncthreads();
@@ -193,11 +197,7 @@ kx0_scatter_kernel(KxArgs<K> a, const uint64_t *__restrict__ bucket_base,
   for_chunk_keys<K>(a, c, [&](bool ok, K key) {
     if (n_stashed < KX_STASH) s.stash[w][n_stashed + lane] = key;  // KX_STASH % 32 == 0
     n_stashed += 32;
-    if (in_smem) {
-      const uint32_t d = ok ? top_digit<K>(key, a.key_bits, D) : 0xFFFFFFFFu;
-      const unsigned peers = __match_any_sync(FULL, d);
-      if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(&s.h[d], (uint32_t)__popc(peers));
-    }
+    if (in_smem && ok) atomicAdd(&s.h[top_digit<K>(key, a.key_bits, D)], 1u);
   });
   if (in_smem) {
     __syncthreads();
@@ -226,16 +226,19 @@ kx0_scatter_kernel(KxArgs<K> a, const uint64_t *__restrict__ bucket_base,
         key = ok ? a.mixer.mix(canonical_kmer<K>(pd.words + woff, j, a.k)) : K(0);
       }
       const uint32_t d = ok ? top_digit<K>(key, a.key_bits, D) : 0xFFFFFFFFu;
-      const unsigned peers = __match_any_sync(FULL, d);
-      const int leader = __ffs(peers) - 1;
-      uint64_t base = 0;
-      if (ok && (int)lane == leader) {
-        if (in_smem) base = bin_base + s.gb[d] + atomicAdd(&s.h[d], (uint32_t)__popc(peers));
-        else base = bucket_base[g0 + d] + atomicAdd(&cursor[g0 + d], (uint32_t)__popc(peers));
+      uint64_t p = 0;
+      if (in_smem) {
+        if (ok) p = bin_base + s.gb[d] + atomicAdd(&s.h[d], 1u);
+      } else {
+        const unsigned peers = __match_any_sync(FULL, d);
+        const int leader = __ffs(peers) - 1;
+        uint64_t base = 0;
+        if (ok && (int)lane == leader)
+          base = bucket_base[g0 + d] + atomicAdd(&cursor[g0 + d], (uint32_t)__popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        p = base + __popc(peers & lanemask_lt());
       }
-      base = __shfl_sync(FULL, base, leader);
       if (ok) {
-        const uint64_t p = base + __popc(peers & lanemask_lt());
         if (p < n_keys) keys[p] = key; else atomicOr(err, ERR_CAPACITY);
       }
     }
@@ -364,10 +367,10 @@ int plan_tiles(Handle &h, const uint32_t *hist, uint64_t NB, const uint32_t *gro
   return KMC_OK;
 }
 
-// Digit bits of a bin with n keys: about TILE/4 keys per bucket.
+// Digit bits of a bin with n keys: about TILE/2 keys per bucket.
 int digits_for(uint64_t n, int key_bits, int tile) {
   int D = 0;
-  while (D < 20 && D < key_bits && (n >> D) > (uint64_t)tile / 4) ++D;
+  while (D < 20 && D < key_bits && (n >> D) > (uint64_t)tile / 2) ++D;
   return D;
 }
 

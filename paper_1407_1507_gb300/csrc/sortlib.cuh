@@ -75,26 +75,50 @@ struct BlockSort {
     uint32_t ws[NW + 1];
   };
 
-  __device__ static void sort(K (&k)[IPT], V (&v)[IPT], int nbits, Smem &s) {
+  // Element layout: the n keys are split evenly over the warps, warp w
+  // holding elements [w*chunk, (w+1)*chunk) with chunk = n/NW rounded up to
+  // a multiple of 32 (at most 32*IPT); slot i of lane l is element
+  // w*chunk + 32*i + l.  Elements past n are neither counted nor written,
+  // so the cost follows the number of keys, not the tile capacity.
+  __device__ static int chunk_of(int n) {
+    int c = (n + NW - 1) / NW;
+    c = (c + 31) & ~31;
+    return c < 32 * IPT ? c : 32 * IPT;
+  }
+  __device__ static int elem(int n, int i) {
+    return (int)(threadIdx.x >> 5) * chunk_of(n) + 32 * i + (int)lane_id();
+  }
+  __device__ static bool valid(int n, int i) {
+    return 32 * i < chunk_of(n) && elem(n, i) < n;
+  }
+
+  __device__ static void sort(K (&k)[IPT], V (&v)[IPT], int nbits, int n, Smem &s) {
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const int chunk = chunk_of(n);
+    const int e_warp = (int)w * chunk;
+    const bool warp_live = e_warp < n;
     for (int bit = 0; bit < nbits; bit += 8) {
       const int nb = nbits - bit < 8 ? nbits - bit : 8;
       for (int i = lane; i < 256; i += 32) s.cnt[w][i] = 0;
       __syncwarp();
       uint32_t rank[IPT];
+      if (warp_live) {
 #pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        unsigned d = KeyTraits<K>::digit(k[i], bit, nb);
-        unsigned peers = __match_any_sync(FULL, d);
-        int leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if ((int)lane == leader) {
-          base = s.cnt[w][d];
-          s.cnt[w][d] = base + __popc(peers);
+        for (int i = 0; i < IPT; ++i) {
+          if (32 * i >= chunk) break;
+          const bool ok = e_warp + i * 32 + (int)lane < n;
+          const unsigned d = ok ? KeyTraits<K>::digit(k[i], bit, nb) : 256u;
+          const unsigned peers = __match_any_sync(FULL, d);
+          const int leader = __ffs(peers) - 1;
+          uint32_t base = 0;
+          if (ok && (int)lane == leader) {
+            base = s.cnt[w][d];
+            s.cnt[w][d] = base + __popc(peers);
+          }
+          base = __shfl_sync(FULL, base, leader);
+          rank[i] = base + __popc(peers & lanemask_lt());
+          __syncwarp();
         }
-        base = __shfl_sync(FULL, base, leader);
-        rank[i] = base + __popc(peers & lanemask_lt());
-        __syncwarp();
       }
       __syncthreads();
       // Exclusive scan of the counters in (digit, warp) order: thread t owns
@@ -111,20 +135,30 @@ struct BlockSort {
         for (int j = 0; j < 8; ++j) { s.cnt[w0 + j][d] = pre; pre += c[j]; }
       }
       __syncthreads();
+      if (warp_live) {
 #pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        unsigned d = KeyTraits<K>::digit(k[i], bit, nb);
-        uint32_t pos = s.cnt[w][d] + rank[i];
-        s.keys[pos] = k[i];
-        if constexpr (HAS_V) s.vals[pos] = v[i];
+        for (int i = 0; i < IPT; ++i) {
+          if (32 * i >= chunk) break;
+          if (e_warp + i * 32 + (int)lane < n) {
+            const unsigned d = KeyTraits<K>::digit(k[i], bit, nb);
+            const uint32_t pos = s.cnt[w][d] + rank[i];
+            s.keys[pos] = k[i];
+            if constexpr (HAS_V) s.vals[pos] = v[i];
+          }
+        }
       }
       __syncthreads();
       if (bit + 8 < nbits) {
+        if (warp_live) {
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-          int e = w * 32 * IPT + i * 32 + lane;
-          k[i] = s.keys[e];
-          if constexpr (HAS_V) v[i] = s.vals[e];
+          for (int i = 0; i < IPT; ++i) {
+            if (32 * i >= chunk) break;
+            const int e = e_warp + i * 32 + lane;
+            if (e < n) {
+              k[i] = s.keys[e];
+              if constexpr (HAS_V) v[i] = s.vals[e];
+            }
+          }
         }
         __syncthreads();
       }
@@ -132,9 +166,11 @@ struct BlockSort {
     if (nbits <= 0) {  // nothing to sort: still leave the keys in smem, in order
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
-        int e = w * 32 * IPT + i * 32 + lane;
-        s.keys[e] = k[i];
-        if constexpr (HAS_V) s.vals[e] = v[i];
+        if (valid(n, i)) {
+          const int e = elem(n, i);
+          s.keys[e] = k[i];
+          if constexpr (HAS_V) s.vals[e] = v[i];
+        }
       }
       __syncthreads();
     }
@@ -323,7 +359,7 @@ struct TileCountSmem {
 // the big list.  If `sorted_out` is not NULL the sorted keys are also
 // written back there (inspection).
 template <typename K, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (THREADS * IPT * sizeof(K) <= 32768) ? 3 : 1)
 tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<K> out,
                   uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys,
                   uint32_t big_cap, uint32_t *err, K *sorted_out) {
@@ -350,11 +386,9 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
     K k[IPT];
     NoVal v[IPT];
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      int e = w * 32 * IPT + i * 32 + lane;
-      k[i] = e < n ? keys[st + e] : KeyTraits<K>::max_key();
-    }
-    BS::sort(k, v, nbits, sm.bs);
+    for (int i = 0; i < IPT; ++i)
+      if (BS::valid(n, i)) k[i] = keys[st + BS::elem(n, i)];
+    BS::sort(k, v, nbits, n, sm.bs);
     if (sorted_out)
       for (int e = threadIdx.x; e < n; e += THREADS) sorted_out[st + e] = sm.bs.keys[e];
     tile_rle<K, THREADS, IPT>(sm.bs.keys, n, sm.heads, sm.bs.ws, &sm.base, out, err);
@@ -398,11 +432,12 @@ tile_pairs_kernel(K *keys, V *vals, TilePlan plan, uint32_t *work, uint32_t *big
     V v[IPT];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-      int e = w * 32 * IPT + i * 32 + lane;
-      k[i] = e < n ? keys[st + e] : KeyTraits<K>::max_key();
-      v[i] = e < n ? vals[st + e] : V();
+      if (BS::valid(n, i)) {
+        k[i] = keys[st + BS::elem(n, i)];
+        v[i] = vals[st + BS::elem(n, i)];
+      }
     }
-    BS::sort(k, v, nbits, sm.bs);
+    BS::sort(k, v, nbits, n, sm.bs);
     for (int e = threadIdx.x; e < n; e += THREADS) {
       keys[st + e] = sm.bs.keys[e];
       vals[st + e] = sm.bs.vals[e];
