@@ -260,6 +260,10 @@ int kmc_count_small_noalloc(const char *d_bases, const uint64_t *d_offsets, uint
 
 #define KMC_DEBUG_KEEP_SUPERKMERS 1u
 #define KMC_DEBUG_KEEP_KEYS 2u
+/* Sorts count tiles on 8 key bits instead of 24, so that distinct keys
+ * sharing their sorted bits become common and the regrouping of such runs
+ * is exercised (tests); the result is the same, only slower. */
+#define KMC_DEBUG_NARROW_SORT 4u
 
 #ifdef __cplusplus
 }

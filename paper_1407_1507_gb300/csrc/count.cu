@@ -303,6 +303,7 @@ int count_tiles(Handle &h, SortScratch &ss, const TilePlan &plan, uint64_t n_key
   out.cx = h.p.cutoff_max;
   out.n_distinct = c64 + 1;
   out.mixer = mixer;
+  out.sort_bits = (h.p.debug_flags & KMC_DEBUG_NARROW_SORT) ? 8 : kCountSortBits;
   static bool attr = false;
   if (!attr) {
     KMC_CUDA_TRY(cudaFuncSetAttribute(tile_count_kernel<K, CNT_THREADS, IPT>,
@@ -353,8 +354,9 @@ int plan_tiles(Handle &h, const uint32_t *hist, uint64_t NB, const uint32_t *gro
       dev_ensure(tmp, scan_tmp_words(NB) * 8, h.st))
     return KMC_ENOMEM;
   KMC_CUDA_TRY(device_excl_scan_u32(hist, as<uint64_t>(base), NB, as<uint64_t>(tmp), h.st));
-  plan_flags_kernel<<<grid_for(NB, 256, 65535), 256, 0, h.st>>>(
-      hist, as<uint64_t>(base), NB, group_base, n_groups, (uint32_t)tile_cap, as<uint32_t>(flags));
+  const uint64_t n_seg = (NB + kGreedySegment - 1) / kGreedySegment;
+  plan_greedy_flags_kernel<<<(unsigned)((n_seg + 7) / 8), 256, 0, h.st>>>(
+      hist, group_base, n_groups, NB, (uint32_t)tile_cap, as<uint32_t>(flags));
   KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
   KMC_CUDA_TRY(device_excl_scan_u32(as<uint32_t>(flags), as<uint64_t>(fscan), NB, as<uint64_t>(tmp), h.st));

@@ -113,6 +113,47 @@ __global__ void plan_flags_kernel(const uint32_t *cnt, const uint64_t *base, uin
   }
 }
 
+// Greedy variant: consecutive buckets join the current tile while it stays
+// within tile_cap keys; a bucket that does not fit starts a new tile (a
+// bucket above tile_cap is a tile alone).  Tiles come out nearly full,
+// which the parallel rule above cannot promise.  The flattened buckets are
+// cut into segments of kGreedySegment; a tile also starts at every segment
+// start and every group start, so each segment is planned by one warp on
+// its own (a huge bin does not serialise the plan).  The warp loads 32
+// counts at a time and every lane replays the same sequential decision over
+// them (shuffles), so the loop stays coalesced and uniform.
+__global__ void plan_greedy_flags_kernel(const uint32_t *__restrict__ cnt,
+                                         const uint32_t *__restrict__ group_base,
+                                         uint32_t n_groups, uint64_t nbk, uint32_t tile_cap,
+                                         uint32_t *__restrict__ flag) {
+  const uint64_t seg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t i0 = seg * kGreedySegment;
+  if (i0 >= nbk) return;  // whole warps leave together
+  const uint64_t i1 = i0 + kGreedySegment < nbk ? i0 + kGreedySegment : nbk;
+  uint64_t acc = 0;
+  for (uint64_t base = i0; base < i1; base += 32) {
+    const uint64_t i = base + lane;
+    uint32_t c = 0;
+    bool gstart = false;
+    if (i < i1) {
+      c = cnt[i];
+      gstart = group_base[group_of(group_base, n_groups, (uint32_t)i)] == (uint32_t)i;
+    }
+    const unsigned gmask = __ballot_sync(0xFFFFFFFFu, gstart);
+    uint32_t mask = 0;
+    const uint32_t lim = i1 - base < 32 ? (uint32_t)(i1 - base) : 32u;
+    for (uint32_t j = 0; j < 32; ++j) {
+      const uint32_t cj = __shfl_sync(0xFFFFFFFFu, c, j);
+      if (j < lim) {
+        const bool start = (base + j == i0) || ((gmask >> j) & 1u) || acc + cj > tile_cap;
+        if (start) { mask |= 1u << j; acc = cj; } else { acc += cj; }
+      }
+    }
+    if (i < i1) flag[i] = (mask >> lane) & 1u;
+  }
+}
+
 __global__ void plan_emit_kernel(const uint32_t *flag, const uint64_t *flag_scan, uint64_t nbk,
                                  uint32_t *tile_first, uint32_t *n_tiles) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nbk;

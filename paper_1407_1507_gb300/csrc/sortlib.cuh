@@ -286,6 +286,7 @@ struct CountOut {
   uint64_t ci, cx;             // inclusive cutoffs (Sect. 2.5)
   unsigned long long *n_distinct;
   Mixer<K> mixer;              // keys in the tiles are mixed; survivors are not
+  int sort_bits;               // tiles are sorted on this many low bits (<= 24)
 };
 
 // Sect. 2.4 "calculates the statistics": run-length count of the sorted keys
@@ -346,6 +347,55 @@ __device__ void tile_rle(const K *s_keys, int n, uint16_t *heads, uint32_t *ws,
   __syncthreads();
 }
 
+// Count mode sorts a tile on the low kCountSortBits bits of its (mixed,
+// uniformly spread) keys only, which already puts equal keys next to each
+// other unless two different keys of the tile share those bits.  Such runs
+// are rare (about t^2/2^25 per tile of t distinct keys) and are repaired by
+// group_equal_runs before counting.
+constexpr int kCountSortBits = 24;
+
+template <typename K>
+__device__ __forceinline__ uint32_t low_bits(K x, int bits) {
+  return (uint32_t)(uint64_t)x & ((1u << bits) - 1u);
+}
+
+// In s[0..n), sorted on the low kCountSortBits bits: every maximal run of
+// equal low bits that holds more than one key value is regrouped so that
+// equal keys are adjacent (one thread per dirty run; O(run x values)).
+template <typename K, int THREADS>
+__device__ void group_equal_runs(K *s, int n, int bits) {
+  bool dirty = false;
+  for (int e = threadIdx.x + 1; e < n; e += THREADS)
+    dirty |= (low_bits(s[e], bits) == low_bits(s[e - 1], bits)) && (s[e] != s[e - 1]);
+  if (!__syncthreads_or(dirty)) return;
+  // thread t handles the dirty runs that start in its stride positions
+  for (int e = threadIdx.x; e < n; e += THREADS) {
+    const bool starts_run = e == 0 || low_bits(s[e], bits) != low_bits(s[e - 1], bits);
+    if (!starts_run) continue;
+    int b = e + 1;
+    bool mixed = false;
+    while (b < n && low_bits(s[b], bits) == low_bits(s[e], bits)) {
+      mixed |= s[b] != s[e];
+      ++b;
+    }
+    if (!mixed) continue;
+    for (int i = e; i < b;) {  // move every copy of s[i] next to it
+      const K key = s[i];
+      int j = i + 1;
+      for (int q = i + 1; q < b; ++q) {
+        if (s[q] == key) {
+          const K t = s[q];
+          s[q] = s[j];
+          s[j] = t;
+          ++j;
+        }
+      }
+      i = j;
+    }
+  }
+  __syncthreads();
+}
+
 template <typename K, int THREADS, int IPT>
 struct TileCountSmem {
   typename BlockSort<K, NoVal, THREADS, IPT>::Smem bs;
@@ -388,7 +438,8 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
 #pragma unroll
     for (int i = 0; i < IPT; ++i)
       if (BS::valid(n, i)) k[i] = keys[st + BS::elem(n, i)];
-    BS::sort(k, v, nbits, n, sm.bs);
+    BS::sort(k, v, nbits < out.sort_bits ? nbits : out.sort_bits, n, sm.bs);
+    if (nbits > out.sort_bits) group_equal_runs<K, THREADS>(sm.bs.keys, n, out.sort_bits);
     if (sorted_out)
       for (int e = threadIdx.x; e < n; e += THREADS) sorted_out[st + e] = sm.bs.keys[e];
     tile_rle<K, THREADS, IPT>(sm.bs.keys, n, sm.heads, sm.bs.ws, &sm.base, out, err);
@@ -674,6 +725,10 @@ big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, K *s
 __global__ void plan_flags_kernel(const uint32_t *cnt, const uint64_t *base, uint64_t nbk,
                                   const uint32_t *group_base, uint32_t n_groups,
                                   uint32_t tile_cap, uint32_t *flag);
+constexpr uint32_t kGreedySegment = 1024;
+__global__ void plan_greedy_flags_kernel(const uint32_t *cnt, const uint32_t *group_base,
+                                         uint32_t n_groups, uint64_t nbk, uint32_t tile_cap,
+                                         uint32_t *flag);
 __global__ void plan_emit_kernel(const uint32_t *flag, const uint64_t *flag_scan, uint64_t nbk,
                                  uint32_t *tile_first, uint32_t *n_tiles);
 

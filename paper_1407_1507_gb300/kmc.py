@@ -28,6 +28,7 @@ KMC_EINPUT = -9
 KMC_AUTO = 0xFFFFFFFF
 KMC_DEBUG_KEEP_SUPERKMERS = 1
 KMC_DEBUG_KEEP_KEYS = 2
+KMC_DEBUG_NARROW_SORT = 4
 
 
 class kmc_params(ctypes.Structure):

@@ -228,3 +228,12 @@ def test_many_pieces_host_and_device(piece_bytes):
     do = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
     with kmc.Counter(28, m=7, n_bins=128, piece_bytes=piece_bytes) as c:
         assert_same(c.add_device(db, do).count().result(), want)
+
+
+@pytest.mark.parametrize("k", [21, 28, 40])
+def test_narrow_tile_sort_regroups_colliding_keys(k):
+    # 8 sorted bits: many distinct keys share them, so runs must be regrouped
+    w = synth.mid(scale=0.002)
+    got = gpu_count(w.bases, w.offsets, k, m=7, n_bins=64, cutoff_min=1,
+                    debug_flags=kmc.KMC_DEBUG_NARROW_SORT)
+    assert_same(got, oracle_count(w.bases, w.offsets, k, 1))
