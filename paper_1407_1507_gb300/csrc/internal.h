@@ -63,6 +63,13 @@ struct SortScratch {
   // global-order pass
   DevBuf o_hist, o_base, o_cursor, o_flags, o_flag_scan, o_tile_first, o_scan_tmp, o_big_list,
       o_big_k, o_big_v;
+  // second level of the (k,x)-mer path: expanded, weighted k-mers
+  DevBuf l2_hist, l2_base, l2_flags, l2_fscan, l2_tfirst, l2_tmp, l2_keys, l2_wts, l2_big,
+      l2_big_k, l2_big_v, l2_grp, l2_counters, l2_out_keys, l2_out_counts;
+  // what kmc_debug_bin_keys needs to find and decode one bin's keys
+  std::vector<uint32_t> dbg_group_base;
+  int dbg_key_bytes = 0;
+  uint64_t dbg_mix[8] = {};  // c lo/hi, cinv lo/hi, mask lo/hi, bits | s1 << 16 | s2 << 32
 };
 
 // Device time per stage: events recorded around launches on the handle's

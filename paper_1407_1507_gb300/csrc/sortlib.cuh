@@ -396,6 +396,43 @@ __device__ void group_equal_runs(K *s, int n, int bits) {
   __syncthreads();
 }
 
+// group_equal_runs for (key, value) pairs: values move with their keys.
+template <typename K, typename V, int THREADS>
+__device__ void group_equal_runs_kv(K *s, V *v, int n, int bits) {
+  bool dirty = false;
+  for (int e = threadIdx.x + 1; e < n; e += THREADS)
+    dirty |= (low_bits(s[e], bits) == low_bits(s[e - 1], bits)) && (s[e] != s[e - 1]);
+  if (!__syncthreads_or(dirty)) return;
+  for (int e = threadIdx.x; e < n; e += THREADS) {
+    const bool starts_run = e == 0 || low_bits(s[e], bits) != low_bits(s[e - 1], bits);
+    if (!starts_run) continue;
+    int b = e + 1;
+    bool mixed = false;
+    while (b < n && low_bits(s[b], bits) == low_bits(s[e], bits)) {
+      mixed |= s[b] != s[e];
+      ++b;
+    }
+    if (!mixed) continue;
+    for (int i = e; i < b;) {
+      const K key = s[i];
+      int j = i + 1;
+      for (int q = i + 1; q < b; ++q) {
+        if (s[q] == key) {
+          const K tk = s[q];
+          s[q] = s[j];
+          s[j] = tk;
+          const V tv = v[q];
+          v[q] = v[j];
+          v[j] = tv;
+          ++j;
+        }
+      }
+      i = j;
+    }
+  }
+  __syncthreads();
+}
+
 template <typename K, int THREADS, int IPT>
 struct TileCountSmem {
   typename BlockSort<K, NoVal, THREADS, IPT>::Smem bs;
@@ -492,6 +529,120 @@ tile_pairs_kernel(K *keys, V *vals, TilePlan plan, uint32_t *work, uint32_t *big
     for (int e = threadIdx.x; e < n; e += THREADS) {
       keys[st + e] = sm.bs.keys[e];
       vals[st + e] = sm.bs.vals[e];
+    }
+    __syncthreads();
+  }
+}
+
+// Weighted count mode: tiles of (key, weight) pairs; equal keys are
+// grouped as in count mode and a key's count is the sum of its weights.
+// Used after expanding distinct (k,x)-mers into their k-mers, each weighted
+// by the (k,x)-mer's multiplicity.
+template <typename K, int THREADS, int IPT>
+struct TileWCountSmem {
+  typename BlockSort<K, uint32_t, THREADS, IPT>::Smem bs;
+  uint16_t heads[THREADS * IPT + 1];
+  unsigned long long wsum[THREADS * IPT + 1];  // wsum[e+1] = weights of elements 0..e
+  unsigned long long ws64[THREADS / 32 + 1];
+  uint32_t tile;
+  unsigned long long base;
+};
+
+template <typename K, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+tile_wcount_kernel(const K *__restrict__ keys, const uint32_t *__restrict__ wts, TilePlan plan,
+                   uint32_t *work, CountOut<K> out, uint32_t *big_list, uint32_t *n_big,
+                   unsigned long long *big_keys, uint32_t big_cap, uint32_t *err) {
+  using BS = BlockSort<K, uint32_t, THREADS, IPT>;
+  using SM = TileWCountSmem<K, THREADS, IPT>;
+  static_assert(BS::TILE < 65536, "heads are 16-bit");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t nt = *plan.n_tiles;
+  for (;;) {
+    const uint32_t t = next_tile(work, &sm.tile);
+    if (t >= nt) break;
+    uint64_t st, en;
+    int nbits;
+    tile_range(plan, t, nt, &st, &en, &nbits);
+    const uint64_t n64 = en - st;
+    if (n64 == 0) continue;
+    if (n64 > (uint64_t)BS::TILE) {
+      if (threadIdx.x == 0) push_big(t, n64, big_list, n_big, big_keys, big_cap, err);
+      continue;
+    }
+    const int n = (int)n64;
+    K k[IPT];
+    uint32_t v[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (BS::valid(n, i)) {
+        k[i] = keys[st + BS::elem(n, i)];
+        v[i] = wts[st + BS::elem(n, i)];
+      }
+    }
+    BS::sort(k, v, nbits < out.sort_bits ? nbits : out.sort_bits, n, sm.bs);
+    if (nbits > out.sort_bits) group_equal_runs_kv<K, uint32_t, THREADS>(sm.bs.keys, sm.bs.vals, n, out.sort_bits);
+    // inclusive prefix sums of the weights (thread-contiguous chunks)
+    const int e0 = threadIdx.x * IPT;
+    unsigned long long loc = 0;
+    for (int j = 0; j < IPT; ++j)
+      if (e0 + j < n) loc += sm.bs.vals[e0 + j];
+    unsigned long long tot64;
+    unsigned long long pre = block_excl_scan<unsigned long long, THREADS>(loc, sm.ws64, &tot64);
+    for (int j = 0; j < IPT; ++j)
+      if (e0 + j < n) { pre += sm.bs.vals[e0 + j]; sm.wsum[e0 + j + 1] = pre; }
+    if (threadIdx.x == 0) sm.wsum[0] = 0;
+    __syncthreads();
+    // heads of runs of equal keys
+    uint32_t nh = 0;
+    for (int j = 0; j < IPT; ++j) {
+      const int e = e0 + j;
+      if (e < n && (e == 0 || sm.bs.keys[e] != sm.bs.keys[e - 1])) ++nh;
+    }
+    uint32_t U;
+    uint32_t hb = block_excl_scan<uint32_t, THREADS>(nh, sm.bs.ws, &U);
+    for (int j = 0; j < IPT; ++j) {
+      const int e = e0 + j;
+      if (e < n && (e == 0 || sm.bs.keys[e] != sm.bs.keys[e - 1])) sm.heads[hb++] = (uint16_t)e;
+    }
+    if (threadIdx.x == 0) sm.heads[U] = (uint16_t)n;
+    __syncthreads();
+    const uint32_t Q = (U + THREADS - 1) / THREADS;
+    const uint32_t u0 = threadIdx.x * Q;
+    uint32_t keep = 0;
+    for (uint32_t j = 0; j < Q; ++j) {
+      const uint32_t u = u0 + j;
+      if (u < U) {
+        const unsigned long long c = sm.wsum[sm.heads[u + 1]] - sm.wsum[sm.heads[u]];
+        const bool kp = c >= out.ci && c <= out.cx;
+        if (kp && c > 0xFFFFFFFFull) atomicOr(err, ERR_OVERFLOW);
+        keep += kp && c <= 0xFFFFFFFFull;
+      }
+    }
+    uint32_t ktot;
+    uint32_t kb = block_excl_scan<uint32_t, THREADS>(keep, sm.bs.ws, &ktot);
+    if (threadIdx.x == 0) {
+      sm.base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
+      atomicAdd(out.n_distinct, (unsigned long long)U);
+    }
+    __syncthreads();
+    const uint64_t base = sm.base;
+    if (base + ktot > out.cap) {
+      if (threadIdx.x == 0) atomicOr(err, ERR_CAPACITY);
+    } else {
+      for (uint32_t j = 0; j < Q; ++j) {
+        const uint32_t u = u0 + j;
+        if (u < U) {
+          const uint32_t h = sm.heads[u];
+          const unsigned long long c = sm.wsum[sm.heads[u + 1]] - sm.wsum[h];
+          if (c >= out.ci && c <= out.cx && c <= 0xFFFFFFFFull) {
+            out.keys[base + kb] = out.mixer.unmix(sm.bs.keys[h]);
+            out.counts[base + kb] = (uint32_t)c;
+            ++kb;
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -611,7 +762,8 @@ __device__ bool big_sort(K *src_k, V *src_v, K *dst_k, V *dst_v, uint64_t n, int
 template <typename K, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
 big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
-                 unsigned long long *scratch_cursor, CountOut<K> out, uint32_t *err) {
+                 unsigned long long *scratch_cursor, CountOut<K> out, uint32_t *err,
+                 K *sorted_out) {
   using SM = BigSmem<K, NoVal, THREADS, IPT>;
   constexpr int CH = THREADS * IPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -628,6 +780,8 @@ big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
   const bool in_scratch = big_sort<K, NoVal, THREADS, IPT>(keys + st, (NoVal *)nullptr, sc,
                                                            (NoVal *)nullptr, n, nbits, sm);
   const K *a = in_scratch ? sc : keys + st;
+  if (sorted_out)
+    for (uint64_t e = threadIdx.x; e < n; e += THREADS) sorted_out[st + e] = a[e];
   // heads: run starts; the run open at the end of a chunk continues in the next
   uint64_t open = 0;  // start of the open run (element 0 always starts one)
   uint32_t *ws = sm.ws;
@@ -717,6 +871,56 @@ big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, K *s
       vals[st + e] = sv[e];
     }
   }
+}
+
+// Weighted count of big tiles: sorted through global scratch, then one
+// thread walks the runs (big tiles of weighted keys are rare).
+template <typename K, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+big_wcount_kernel(K *keys, uint32_t *wts, TilePlan plan, const uint32_t *big_list, K *scratch_k,
+                  uint32_t *scratch_v, unsigned long long *scratch_cursor, CountOut<K> out,
+                  uint32_t *err) {
+  using SM = BigSmem<K, uint32_t, THREADS, IPT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t t = big_list[blockIdx.x];
+  const uint32_t nt = *plan.n_tiles;
+  uint64_t st, en;
+  int nbits;
+  tile_range(plan, t, nt, &st, &en, &nbits);
+  const uint64_t n = en - st;
+  if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
+  __syncthreads();
+  K *sk = scratch_k + sm.base;
+  uint32_t *sv = scratch_v + sm.base;
+  const bool in_scratch = big_sort<K, uint32_t, THREADS, IPT>(keys + st, wts + st, sk, sv, n, nbits, sm);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const K *a = in_scratch ? sk : keys + st;
+  const uint32_t *w = in_scratch ? sv : wts + st;
+  unsigned long long runs = 0;
+  uint64_t i = 0;
+  while (i < n) {
+    uint64_t j = i;
+    unsigned long long c = 0;
+    while (j < n && a[j] == a[i]) c += w[j++];
+    ++runs;
+    if (c >= out.ci && c <= out.cx) {
+      if (c > 0xFFFFFFFFull) {
+        atomicOr(err, ERR_OVERFLOW);
+      } else {
+        const unsigned long long p = atomicAdd(out.n, 1ull);
+        if (p < out.cap) {
+          out.keys[p] = out.mixer.unmix(a[i]);
+          out.counts[p] = (uint32_t)c;
+        } else {
+          atomicOr(err, ERR_CAPACITY);
+        }
+      }
+    }
+    i = j;
+  }
+  atomicAdd(out.n_distinct, runs);
 }
 
 // ---------------------------------------------------------------- plan kernels

@@ -237,3 +237,67 @@ def test_narrow_tile_sort_regroups_colliding_keys(k):
     got = gpu_count(w.bases, w.offsets, k, m=7, n_bins=64, cutoff_min=1,
                     debug_flags=kmc.KMC_DEBUG_NARROW_SORT)
     assert_same(got, oracle_count(w.bases, w.offsets, k, 1))
+
+
+# ------------------------------------------------------------------ (k,x)-mers
+
+@pytest.mark.parametrize("x", [1, 2, 3])
+@pytest.mark.parametrize("seed", range(4))
+def test_kx_random_small_inputs(x, seed):
+    rng = random.Random(5000 + 10 * x + seed)
+    k = rng.choice([1, 3, 9, 15, 21, 28, 29, 31, 32, 33, 55, 60, 63])
+    m = rng.choice([3, 5, 7, 9])
+    reads = rand_reads(rng, rng.randint(1, 250), 0, rng.choice([60, 150, 300]),
+                       p_n=rng.choice([0.0, 0.02]), alphabet=rng.choice(["ACGT", "AC"]))
+    ci = rng.choice([1, 2])
+    b, o = oracle.as_reads(reads)
+    got = gpu_count(b, o, k, m=m, n_bins=rng.choice([1, 16, 512]), x=x, cutoff_min=ci)
+    assert_same(got, oracle_count(b, o, k, ci))
+
+
+@pytest.mark.parametrize("k,x", [(21, 3), (28, 1), (28, 2), (28, 3), (31, 3), (55, 3)])
+def test_kx_mid_workload_scaled(k, x):
+    w = synth.mid(scale=0.003)
+    with kmc.Counter(k, m=7, n_bins=512, x=x) as c:
+        got = c.add(w.bases, w.offsets).count().result()
+        st = c.stats()
+    assert st["x_used"] == x
+    assert st["n_sorted_keys"] < st["n_kmer_positions"]  # fewer strings to sort (Sect. 2.3)
+    assert_same(got, oracle_count(w.bases, w.offsets, k))
+
+
+def test_kx_big_and_narrow_paths():
+    rng = random.Random(11)
+    r = "".join(rng.choice("ACGT") for _ in range(70))
+    reads = [r] * 20000 + ["A" * 90] * 500 + rand_reads(rng, 400, 30, 150)
+    b, o = oracle.as_reads(reads)
+    for flags in (0, kmc.KMC_DEBUG_NARROW_SORT):
+        got = gpu_count(b, o, 25, m=7, n_bins=4, x=3, debug_flags=flags)
+        assert_same(got, oracle_count(b, o, 25))
+
+
+def _kx_key(value, xp, k, x):
+    return (xp << (2 * (k + x))) | (value << (2 * (x - xp)))
+
+
+@pytest.mark.parametrize("k,x", [(28, 3), (21, 1), (40, 2)])
+def test_kx_keys_per_bin_match_oracle_split(k, x):
+    # the bins' (k,x)-mer multisets equal the oracle's Sect. 2.3 split of the
+    # oracle's super k-mers (same 128-position cut), binned by the same map
+    w = synth.mid(scale=0.0004)
+    m, B = 7, 8
+    mp = (np.arange(4 ** m + 1) % B).astype(np.uint32)
+    with kmc.Counter(k, m=m, n_bins=B, x=x, debug_flags=kmc.KMC_DEBUG_KEEP_KEYS) as c:
+        kmc.kmc_set_bin_map(c.h, mp)
+        c.add(w.bases, w.offsets).count()
+        got = {b: sorted(oracle.kmers_to_int(kmc.kmc_debug_bin_keys(c.h, b))) for b in range(B)}
+    want = {b: [] for b in range(B)}
+    for r in range(w.n_reads):
+        a, e = int(w.offsets[r]), int(w.offsets[r + 1])
+        read = bytes(w.bases[a:e]).decode()
+        for st, n, g in oracle.superkmers(read, k, m, cut_every=128):
+            sk = read[st:st + n + k - 1]
+            for _, xp, _, v in oracle.kxmers(sk, k, x):
+                want[int(mp[g])].append(_kx_key(v, xp, k, x))
+    for b in range(B):
+        assert got[b] == sorted(want[b]), f"bin {b}"
