@@ -221,6 +221,51 @@ int kmc_debug_superkmers(kmc_handle *h, uint64_t *read_index, uint32_t *pos, uin
 int kmc_debug_bin_keys(kmc_handle *h, uint32_t bin, uint64_t *keys, uint64_t capacity,
                        uint64_t *n_out, uint32_t *words_per_key);
 
+/* ---------------------------------------------------------- batches
+ * Many independent read sets counted together.  A sub-batch packs whole sets
+ * into one input stream; set s owns its own range of bins, so the sets never
+ * mix (the counts of each set are exactly what kmc_count gives for it alone).
+ * All buffers are sized from the capacity given at open, and the launch
+ * sequence of a sub-batch reads every data-dependent size from device memory,
+ * so it runs without host synchronisation: it is captured once as a CUDA
+ * graph and replayed for every sub-batch of the same k.  A set larger than
+ * the capacity is counted by the single-set path.  With KMC_BATCH_AUTOTUNE
+ * the first sub-batch of each k times a few settings (bins per set, bucket
+ * width, tile size) and the fastest is kept for the handle's lifetime.
+ *
+ * kmc_batch_open: base parameters (k is given per set; m, n_bins (ignored:
+ *   tuned), cutoffs, device, stream as in kmc_params; x must be 0 or
+ *   KMC_AUTO), capacity of one sub-batch: max_bases (1 KiB .. 2 GiB) bytes,
+ *   max_reads reads, max_sets sets (<= 65536).  Device memory of about
+ *   60 bytes per byte of capacity is allocated per k in use.
+ * kmc_batch_run: counts n_sets host read sets (each as in kmc_add_reads;
+ *   k[s] in 1..32).  Blocks.  Results replace those of the previous run.
+ * kmc_batch_result: host arrays of set `set` (owned by the handle, valid
+ *   until the next run or close): n k-mers (one uint64 each, layout as in
+ *   kmc_result) ascending, and their counts. */
+#define KMC_BATCH_AUTOTUNE 1u
+#define KMC_BATCH_NO_GRAPH 2u
+typedef struct kmc_batch kmc_batch;
+typedef struct {
+  float ms_device;          /* device time of the sub-batches (CUDA events)   */
+  float ms_wall;            /* wall time of the last kmc_batch_run            */
+  uint32_t n_sub_batches;   /* sub-batches run (graph replays)                */
+  uint32_t n_single;        /* sets counted by the single-set path            */
+  uint32_t tuning_runs;     /* sub-batch runs spent by the autotuner          */
+  uint32_t bins_per_set;    /* tuning in use (last k)                         */
+  uint32_t tile_keys;
+  uint32_t bucket_keys;
+  uint64_t n_kmers_out;     /* k-mers in all results                          */
+} kmc_batch_stats;
+int kmc_batch_open(kmc_batch **b, const kmc_params *p, uint64_t max_bases, uint64_t max_reads,
+                   uint32_t max_sets, uint32_t flags);
+int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
+                  const uint64_t *const *offsets, const uint64_t *n_reads, const uint32_t *k);
+int kmc_batch_result(kmc_batch *b, uint32_t set, const uint64_t **kmers, const uint32_t **counts,
+                     uint64_t *n);
+int kmc_batch_stats_get(const kmc_batch *b, kmc_batch_stats *s);
+void kmc_batch_close(kmc_batch *b);
+
 /* ---------------------------------------------------------- no allocation
  * The paper has no counterpart to this entry point; it serves callers that
  * must not allocate GPU memory.  Examples: code that runs while a CUDA graph

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmc.so")
-SOURCES = ["api.cu", "distribute.cu", "count.cu", "order.cu", "scan.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "sortlib.cuh", "internal.h"]
+SOURCES = ["api.cu", "distribute.cu", "count.cu", "order.cu", "scan.cu", "noalloc.cu", "batch.cu"]
+HEADERS = ["common.cuh", "sortlib.cuh", "internal.h", "dist_kernels.cuh", "kx_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -142,7 +142,7 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
   if (nbig) {
     // the original arrays serve as the scratch of the big buckets
     big_pairs_kernel<K, V, PAIR_THREADS, PAIR_BIG_IPT><<<nbig, PAIR_THREADS, sizeof(BSM), h.st>>>(
-        tk, tv, plan, as<uint32_t>(ss.o_flags), keys, vals, c64 + 1); KMC_COUNT_LAUNCH();
+        tk, tv, plan, as<uint32_t>(ss.o_flags), c32 + 1, keys, vals, c64 + 1); KMC_COUNT_LAUNCH();
     KMC_CUDA_TRY(cudaGetLastError());
   }
   KMC_CUDA_TRY(cudaMemcpyAsync(keys, tk, n * sizeof(K), cudaMemcpyDeviceToDevice, h.st));

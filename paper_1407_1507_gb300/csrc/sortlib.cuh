@@ -218,7 +218,8 @@ __device__ __forceinline__ uint32_t group_of(const uint32_t *group_base, uint32_
 
 // Key range of tile t and the number of low key bits that vary inside it.
 __device__ __forceinline__ void tile_range(const TilePlan &p, uint32_t t, uint32_t nt,
-                                           uint64_t *start, uint64_t *end, int *nbits) {
+                                           uint64_t *start, uint64_t *end, int *nbits,
+                                           uint32_t *group = nullptr) {
   const uint32_t i = p.tile_first[t];
   const uint32_t j = (t + 1 < nt) ? p.tile_first[t + 1] : p.NB;  // one past the last bucket
   *start = p.bucket_base[i];
@@ -226,6 +227,7 @@ __device__ __forceinline__ void tile_range(const TilePlan &p, uint32_t t, uint32
   const uint32_t g = group_of(p.group_base, p.n_groups, i);
   const uint32_t d0 = i - p.group_base[g], d1 = j - 1 - p.group_base[g];
   *nbits = tile_sort_bits(p.key_bits, p.group_D[g], d0, d1);
+  if (group) *group = g;
 }
 
 // Optional bijective mix of the keys (2^bits values onto themselves): the
@@ -287,13 +289,16 @@ struct CountOut {
   unsigned long long *n_distinct;
   Mixer<K> mixer;              // keys in the tiles are mixed; survivors are not
   int sort_bits;               // tiles are sorted on this many low bits (<= 24)
+  uint32_t *slots;             // batches: set of each survivor (group / bins_per_slot), else NULL
+  uint32_t bins_per_slot;
 };
 
 // Sect. 2.4 "calculates the statistics": run-length count of the sorted keys
 // s_keys[0..n) of one tile, keep counts in [ci, cx], append to `out`.
 template <typename K, int THREADS, int IPT>
 __device__ void tile_rle(const K *s_keys, int n, uint16_t *heads, uint32_t *ws,
-                         unsigned long long *s_base, const CountOut<K> &out, uint32_t *err) {
+                         unsigned long long *s_base, const CountOut<K> &out, uint32_t *err,
+                         uint32_t group) {
   const int e0 = threadIdx.x * IPT;
   uint32_t nh = 0;
 #pragma unroll 4
@@ -339,6 +344,7 @@ __device__ void tile_rle(const K *s_keys, int n, uint16_t *heads, uint32_t *ws,
         if (c >= out.ci && c <= out.cx) {
           out.keys[base + kb] = out.mixer.unmix(s_keys[h]);
           out.counts[base + kb] = c;
+          if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
           ++kb;
         }
       }
@@ -462,7 +468,8 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
     if (t >= nt) break;
     uint64_t st, en;
     int nbits;
-    tile_range(plan, t, nt, &st, &en, &nbits);
+    uint32_t group;
+    tile_range(plan, t, nt, &st, &en, &nbits, &group);
     const uint64_t n64 = en - st;
     if (n64 == 0) continue;
     if (n64 > (uint64_t)BS::TILE) {
@@ -479,7 +486,7 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
     if (nbits > out.sort_bits) group_equal_runs<K, THREADS>(sm.bs.keys, n, out.sort_bits);
     if (sorted_out)
       for (int e = threadIdx.x; e < n; e += THREADS) sorted_out[st + e] = sm.bs.keys[e];
-    tile_rle<K, THREADS, IPT>(sm.bs.keys, n, sm.heads, sm.bs.ws, &sm.base, out, err);
+    tile_rle<K, THREADS, IPT>(sm.bs.keys, n, sm.heads, sm.bs.ws, &sm.base, out, err, group);
   }
 }
 
@@ -761,18 +768,21 @@ __device__ bool big_sort(K *src_k, V *src_v, K *dst_k, V *dst_v, uint64_t n, int
 // chunk by chunk, carrying the open run across chunks.
 template <typename K, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
-big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
-                 unsigned long long *scratch_cursor, CountOut<K> out, uint32_t *err,
+big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, const uint32_t *n_big,
+                 K *scratch, unsigned long long *scratch_cursor, CountOut<K> out, uint32_t *err,
                  K *sorted_out) {
   using SM = BigSmem<K, NoVal, THREADS, IPT>;
   constexpr int CH = THREADS * IPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &sm = *reinterpret_cast<SM *>(smem_raw);
-  const uint32_t t = big_list[blockIdx.x];
   const uint32_t nt = *plan.n_tiles;
+  const uint32_t nbig = *n_big;
+  for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+  const uint32_t t = big_list[bi];
   uint64_t st, en;
   int nbits;
-  tile_range(plan, t, nt, &st, &en, &nbits);
+  uint32_t group;
+  tile_range(plan, t, nt, &st, &en, &nbits, &group);
   const uint64_t n = en - st;
   if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
   __syncthreads();
@@ -835,6 +845,7 @@ big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
           if (c >= out.ci && c <= out.cx && c <= 0xFFFFFFFFull) {
             out.keys[base + kb] = out.mixer.unmix(a[rs]);
             out.counts[base + kb] = (uint32_t)c;
+            if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
             ++kb;
           }
         }
@@ -845,18 +856,22 @@ big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, K *scratch,
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(out.n_distinct, n_runs);
+  __syncthreads();
+  }
 }
 
 // Pairs mode big tiles: sort; copy back if the result ended in scratch.
 template <typename K, typename V, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
-big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, K *scratch_k,
-                 V *scratch_v, unsigned long long *scratch_cursor) {
+big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, const uint32_t *n_big,
+                 K *scratch_k, V *scratch_v, unsigned long long *scratch_cursor) {
   using SM = BigSmem<K, V, THREADS, IPT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &sm = *reinterpret_cast<SM *>(smem_raw);
-  const uint32_t t = big_list[blockIdx.x];
   const uint32_t nt = *plan.n_tiles;
+  const uint32_t nbig = *n_big;
+  for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+  const uint32_t t = big_list[bi];
   uint64_t st, en;
   int nbits;
   tile_range(plan, t, nt, &st, &en, &nbits);
@@ -870,6 +885,8 @@ big_pairs_kernel(K *keys, V *vals, TilePlan plan, const uint32_t *big_list, K *s
       keys[st + e] = sk[e];
       vals[st + e] = sv[e];
     }
+  }
+  __syncthreads();
   }
 }
 

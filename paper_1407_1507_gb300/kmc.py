@@ -65,6 +65,23 @@ STAGES = ["pack", "signature", "bin_scatter", "bin_map", "kx_count", "plan", "kx
           "tile_sort", "big_sort", "order", "other"]
 
 
+class kmc_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("ms_device", ctypes.c_float), ("ms_wall", ctypes.c_float),
+        ("n_sub_batches", ctypes.c_uint32), ("n_single", ctypes.c_uint32),
+        ("tuning_runs", ctypes.c_uint32), ("bins_per_set", ctypes.c_uint32),
+        ("tile_keys", ctypes.c_uint32), ("bucket_keys", ctypes.c_uint32),
+        ("n_kmers_out", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+KMC_BATCH_AUTOTUNE = 1
+KMC_BATCH_NO_GRAPH = 2
+
+
 class KmcError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"{what}: {strerror(code)} ({code})")
@@ -94,6 +111,14 @@ SIGNATURES = [
     ("kmc_get_bin_map", ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
     ("kmc_debug_superkmers", ctypes.c_int, [_vp, _u64p, _u32p, _u32p, _u32p, ctypes.c_uint64, _u64p]),
     ("kmc_debug_bin_keys", ctypes.c_int, [_vp, ctypes.c_uint32, _u64p, ctypes.c_uint64, _u64p, _u32p]),
+    ("kmc_batch_open", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(kmc_params), ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]),
+    ("kmc_batch_run", ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                     _u64p, _u32p]),
+    ("kmc_batch_result", ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                        _u64p]),
+    ("kmc_batch_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_batch_stats)]),
+    ("kmc_batch_close", None, [_vp]),
     ("kmc_count_small_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64,
                                                _vp, _vp]),
@@ -259,6 +284,48 @@ def kmc_count_small_noalloc(d_bases_ptr, d_offsets_ptr, n_reads, n_bases, k, cut
     _check(load().kmc_count_small_noalloc(d_bases_ptr, d_offsets_ptr, n_reads, n_bases, k,
                                           cutoff_min, cutoff_max, d_kmers_ptr, d_counts_ptr,
                                           capacity, d_n_out_ptr, stream), "kmc_count_small_noalloc")
+
+
+def kmc_batch_open(p: kmc_params, max_bases: int, max_reads: int, max_sets: int, flags: int = 0) -> int:
+    h = _vp()
+    _check(load().kmc_batch_open(ctypes.byref(h), ctypes.byref(p), max_bases, max_reads, max_sets, flags),
+           "kmc_batch_open")
+    return h.value
+
+
+def kmc_batch_run(b, sets, ks):
+    """sets: list of (bases uint8 array, offsets uint64 array); ks: k per set."""
+    n = len(sets)
+    keep = [(np.ascontiguousarray(bs, dtype=np.uint8), np.ascontiguousarray(of, dtype=np.uint64))
+            for bs, of in sets]
+    bp = (_vp * max(n, 1))(*[x[0].ctypes.data for x in keep])
+    op = (_vp * max(n, 1))(*[x[1].ctypes.data for x in keep])
+    nr = np.array([x[1].size - 1 for x in keep] or [0], dtype=np.uint64)
+    kk = np.array(list(ks) or [0], dtype=np.uint32)
+    _check(load().kmc_batch_run(b, n, bp, op, _ptr(nr, ctypes.c_uint64), _ptr(kk, ctypes.c_uint32)),
+           "kmc_batch_run")
+
+
+def kmc_batch_result(b, s: int):
+    dk, dc, n = _vp(), _vp(), ctypes.c_uint64()
+    _check(load().kmc_batch_result(b, s, ctypes.byref(dk), ctypes.byref(dc), ctypes.byref(n)),
+           "kmc_batch_result")
+    if n.value == 0:
+        return np.zeros((0, 1), np.uint64), np.zeros(0, np.uint32)
+    kms = np.ctypeslib.as_array(ctypes.cast(dk.value, _u64p), shape=(n.value,)).copy().reshape(-1, 1)
+    cnt = np.ctypeslib.as_array(ctypes.cast(dc.value, _u32p), shape=(n.value,)).copy()
+    return kms, cnt
+
+
+def kmc_batch_stats_get(b) -> dict:
+    s = kmc_batch_stats()
+    _check(load().kmc_batch_stats_get(b, ctypes.byref(s)), "kmc_batch_stats_get")
+    return s.as_dict()
+
+
+def kmc_batch_close(b):
+    if b:
+        load().kmc_batch_close(b)
 
 
 # ----------------------------------------------------------- convenience
