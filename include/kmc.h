@@ -266,6 +266,57 @@ int kmc_batch_result(kmc_batch *b, uint32_t set, const uint64_t **kmers, const u
 int kmc_batch_stats_get(const kmc_batch *b, kmc_batch_stats *s);
 void kmc_batch_close(kmc_batch *b);
 
+/* ---------------------------------------------------------- serving
+ * A request loop with continuous batching.  kmc_server_submit copies a
+ * job's host reads and queues it (it never blocks on the GPU).  n_workers
+ * worker threads, each with its own CUDA stream and resident batch engines
+ * (kmc_batch_*), repeatedly admit queued jobs in arrival order while they
+ * fit one batch (batch_bases bytes, batch_reads reads, batch_sets jobs) and
+ * the device-memory budget: the predicted footprint of a job is 64 bytes
+ * per input byte, and the jobs in flight never exceed mem_budget (a job is
+ * always admitted when nothing is in flight).  Jobs that arrive while
+ * batches run join the next batch that has room.  A job's result is exactly
+ * what kmc_count gives for its reads alone.
+ * kmc_server_wait: KMC_OK when done, KMC_EAGAIN on timeout (timeout_s < 0
+ *   waits without limit), or the job's error code.
+ * kmc_server_result: host arrays owned by the server until
+ *   kmc_server_release; latency = completion - submission (wall clock).
+ * kmc_server_stats_get: completed jobs, p50 / p99 / mean latency, batches,
+ *   the largest batch, the most jobs in flight, wall time from the first
+ *   submission to the last completion. */
+typedef struct kmc_server kmc_server;
+typedef struct {
+  kmc_params base;       /* m, cutoffs, device (k is given per job; x = 0)  */
+  uint64_t batch_bases;  /* capacity of one batch, bytes (0 = 128 MiB)      */
+  uint64_t batch_reads;  /* reads per batch (0 = batch_bases / 64)          */
+  uint32_t batch_sets;   /* jobs per batch (0 = 256)                        */
+  uint32_t n_workers;    /* batches in flight, 1..8 (0 = 2)                 */
+  uint64_t mem_budget;   /* predicted device bytes in flight (0 = workers x
+                            64 x batch_bases)                               */
+  uint32_t batch_flags;  /* KMC_BATCH_* for the workers' batch handles      */
+  uint32_t reserved0;
+} kmc_server_cfg;
+typedef struct {
+  uint64_t jobs_done;
+  uint64_t jobs_queued;
+  uint64_t batches;
+  uint64_t max_batch_jobs;
+  uint64_t max_inflight_jobs;
+  double p50_ms, p99_ms, mean_ms;
+  double wall_s;
+  int32_t error;          /* last job error (0 = none)                      */
+  int32_t reserved0;
+} kmc_server_stats;
+int kmc_server_open(kmc_server **s, const kmc_server_cfg *cfg);
+int kmc_server_submit(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets,
+                      uint64_t n_reads, uint64_t *job_id);
+int kmc_server_wait(kmc_server *s, uint64_t job_id, double timeout_s);
+int kmc_server_result(kmc_server *s, uint64_t job_id, const uint64_t **kmers,
+                      const uint32_t **counts, uint64_t *n, double *latency_ms);
+int kmc_server_release(kmc_server *s, uint64_t job_id);
+int kmc_server_stats_get(kmc_server *s, kmc_server_stats *st);
+void kmc_server_close(kmc_server *s);
+
 /* ---------------------------------------------------------- no allocation
  * The paper has no counterpart to this entry point; it serves callers that
  * must not allocate GPU memory.  Examples: code that runs while a CUDA graph

@@ -1,0 +1,316 @@
+// Served counting: a request loop with continuous batching.
+//
+// kmc_server_submit copies a job's reads into host memory and queues it.
+// Worker threads, each owning a batch handle (its own CUDA stream and its
+// resident, graph-captured engines), loop: take from the head of the queue
+// as many jobs as fit one batch (bases, reads, sets) and the device-memory
+// budget (the predicted footprint of every job in flight), count them as one
+// batch, publish each job's result and latency, and come back for more.  A
+// job that arrives while batches run is admitted into the next batch whose
+// capacity and memory allow it; two workers keep one batch's host work
+// (copies, result split) overlapped with another's kernels.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace kmc {
+namespace {
+
+// Predicted device bytes per input byte while a job is counted: the
+// distribution and sort buffers scale with the input (2-bit codes and
+// masks, super k-mer list and bins, keys, survivors).
+constexpr uint64_t kFootprintPerBase = 64;
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Job {
+  uint64_t id = 0;
+  uint32_t k = 0;
+  std::vector<char> bases;
+  std::vector<uint64_t> offsets;
+  uint64_t n_reads = 0;
+  uint64_t footprint = 0;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  int status = 0;  // 0 queued, 1 running, 2 done, < 0 error code
+  std::vector<uint64_t> kmers;
+  std::vector<uint32_t> counts;
+};
+
+}  // namespace
+}  // namespace kmc
+
+using namespace kmc;
+
+struct kmc_server {
+  kmc_server_cfg cfg{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job *> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Job>> jobs;
+  uint64_t next_id = 1;
+  uint64_t inflight = 0;        // predicted bytes of jobs being counted
+  uint64_t inflight_jobs = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<kmc_batch *> batches;
+  // statistics
+  std::vector<double> lat_ms;
+  uint64_t done = 0, n_batches = 0, max_batch_jobs = 0, max_inflight_jobs = 0;
+  double t_first = 0, t_last = 0;
+  int error = 0;
+};
+
+namespace {
+
+bool fits(const kmc_server &s, const std::vector<Job *> &take, uint64_t nb, uint64_t nr, uint64_t fp,
+          const Job &j) {
+  const kmc_server_cfg &c = s.cfg;
+  const uint64_t jb = j.offsets.back();
+  if (s.inflight + fp + j.footprint > c.mem_budget && !(take.empty() && s.inflight == 0)) return false;
+  if (take.empty()) return true;  // a job always fits an empty batch (large ones run alone)
+  if (take.size() >= c.batch_sets) return false;
+  return nb + jb + 64 <= c.batch_bases && nr + j.n_reads + 1 <= c.batch_reads;
+}
+
+void worker(kmc_server *s, int w) {
+  kmc_batch *b = s->batches[w];
+  cudaSetDevice(s->cfg.base.device);
+  for (;;) {
+    std::vector<Job *> take;
+    uint64_t fp = 0;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+      if (s->queue.empty()) {
+        if (s->stop) return;
+        continue;
+      }
+      // continuous batching: admit queued jobs in arrival order while they fit
+      uint64_t nb = 0, nr = 0;
+      while (!s->queue.empty()) {
+        Job *j = s->queue.front();
+        if (!fits(*s, take, nb, nr, fp, *j)) break;
+        take.push_back(j);
+        s->queue.pop_front();
+        nb += j->offsets.back();
+        nr += j->n_reads;
+        fp += j->footprint;
+        if (nb + 64 > s->cfg.batch_bases) break;  // a large job runs alone
+      }
+      if (take.empty()) {  // nothing fits the memory budget yet: wait for a batch to finish
+        s->cv_work.wait(lk, [&] { return s->stop || s->inflight == 0; });
+        continue;
+      }
+      s->inflight += fp;
+      s->inflight_jobs += take.size();
+      s->max_inflight_jobs = std::max(s->max_inflight_jobs, s->inflight_jobs);
+      const double t = now_s();
+      for (Job *j : take) {
+        j->status = 1;
+        j->t_start = t;
+      }
+    }
+    std::vector<const char *> bp;
+    std::vector<const uint64_t *> op;
+    std::vector<uint64_t> nr;
+    std::vector<uint32_t> ks;
+    for (Job *j : take) {
+      bp.push_back(j->bases.data());
+      op.push_back(j->offsets.data());
+      nr.push_back(j->n_reads);
+      ks.push_back(j->k);
+    }
+    int rc = kmc_batch_run(b, (uint32_t)take.size(), bp.data(), op.data(), nr.data(), ks.data());
+    std::vector<std::vector<uint64_t>> rk(take.size());
+    std::vector<std::vector<uint32_t>> rcnt(take.size());
+    if (rc == KMC_OK) {
+      for (uint32_t i = 0; i < take.size(); ++i) {
+        const uint64_t *kp = nullptr;
+        const uint32_t *cp = nullptr;
+        uint64_t n = 0;
+        kmc_batch_result(b, i, &kp, &cp, &n);
+        rk[i].assign(kp, kp + n);
+        rcnt[i].assign(cp, cp + n);
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      const double t = now_s();
+      for (uint32_t i = 0; i < take.size(); ++i) {
+        Job *j = take[i];
+        j->t_done = t;
+        if (rc == KMC_OK) {
+          j->kmers.swap(rk[i]);
+          j->counts.swap(rcnt[i]);
+          j->status = 2;
+          s->lat_ms.push_back((j->t_done - j->t_submit) * 1e3);
+          s->done += 1;
+        } else {
+          j->status = rc;
+          s->error = rc;
+        }
+        std::vector<char>().swap(j->bases);  // the reads are no longer needed
+        std::vector<uint64_t>().swap(j->offsets);
+        j->offsets.push_back(0);
+      }
+      s->inflight -= fp;
+      s->inflight_jobs -= take.size();
+      s->n_batches += 1;
+      s->max_batch_jobs = std::max<uint64_t>(s->max_batch_jobs, take.size());
+      s->t_last = t;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+}
+
+double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * (double)(v.size() - 1);
+  const size_t i = (size_t)pos;
+  const double f = pos - (double)i;
+  return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+int kmc_server_open(kmc_server **out, const kmc_server_cfg *cfg) {
+  if (!out || !cfg) return KMC_EINVAL;
+  *out = nullptr;
+  kmc_server_cfg c = *cfg;
+  if (c.n_workers == 0) c.n_workers = 2;
+  if (c.n_workers > 8) return KMC_EINVAL;
+  if (c.batch_sets == 0) c.batch_sets = 256;
+  if (c.batch_bases == 0) c.batch_bases = 128ull << 20;
+  if (c.batch_reads == 0) c.batch_reads = c.batch_bases / 64;
+  if (c.mem_budget == 0) c.mem_budget = (uint64_t)c.n_workers * kFootprintPerBase * c.batch_bases;
+  auto *s = new kmc_server();
+  s->cfg = c;
+  for (uint32_t w = 0; w < c.n_workers; ++w) {
+    kmc_params p = c.base;
+    p.cuda_stream = nullptr;  // every worker runs on a stream of its own
+    kmc_batch *b = nullptr;
+    int rc = kmc_batch_open(&b, &p, c.batch_bases, c.batch_reads, c.batch_sets, c.batch_flags);
+    if (rc) {
+      for (kmc_batch *x : s->batches) kmc_batch_close(x);
+      delete s;
+      return rc;
+    }
+    s->batches.push_back(b);
+  }
+  for (uint32_t w = 0; w < c.n_workers; ++w) s->workers.emplace_back(worker, s, (int)w);
+  *out = s;
+  return KMC_OK;
+}
+
+int kmc_server_submit(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets,
+                      uint64_t n_reads, uint64_t *job_id) {
+  if (!s || !offsets || !job_id || k < 1 || k > 32) return KMC_EINVAL;
+  if (offsets[0] != 0) return KMC_EINPUT;
+  for (uint64_t r = 0; r < n_reads; ++r)
+    if (offsets[r + 1] < offsets[r]) return KMC_EINPUT;
+  const uint64_t nb = offsets[n_reads];
+  if (nb && !bases) return KMC_EINVAL;
+  auto j = std::make_unique<Job>();
+  j->k = k;
+  j->bases.assign(bases, bases + nb);
+  j->offsets.assign(offsets, offsets + n_reads + 1);
+  j->n_reads = n_reads;
+  j->footprint = kFootprintPerBase * (nb + 64);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return KMC_ESTATE;
+    j->id = s->next_id++;
+    j->t_submit = now_s();
+    if (s->t_first == 0) s->t_first = j->t_submit;
+    *job_id = j->id;
+    s->queue.push_back(j.get());
+    s->jobs[j->id] = std::move(j);
+  }
+  s->cv_work.notify_one();
+  return KMC_OK;
+}
+
+int kmc_server_wait(kmc_server *s, uint64_t job_id, double timeout_s) {
+  if (!s) return KMC_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return KMC_EINVAL;
+  Job *j = it->second.get();
+  const auto pred = [&] { return j->status == 2 || j->status < 0; };
+  if (timeout_s < 0) s->cv_done.wait(lk, pred);
+  else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) return KMC_EAGAIN;
+  return j->status < 0 ? j->status : KMC_OK;
+}
+
+int kmc_server_result(kmc_server *s, uint64_t job_id, const uint64_t **kmers, const uint32_t **counts,
+                      uint64_t *n, double *latency_ms) {
+  if (!s) return KMC_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return KMC_EINVAL;
+  Job *j = it->second.get();
+  if (j->status < 0) return j->status;
+  if (j->status != 2) return KMC_EAGAIN;
+  if (kmers) *kmers = j->kmers.data();
+  if (counts) *counts = j->counts.data();
+  if (n) *n = j->kmers.size();
+  if (latency_ms) *latency_ms = (j->t_done - j->t_submit) * 1e3;
+  return KMC_OK;
+}
+
+int kmc_server_release(kmc_server *s, uint64_t job_id) {
+  if (!s) return KMC_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return KMC_EINVAL;
+  if (it->second->status < 2 && it->second->status >= 0) return KMC_ESTATE;
+  s->jobs.erase(it);
+  return KMC_OK;
+}
+
+int kmc_server_stats_get(kmc_server *s, kmc_server_stats *st) {
+  if (!s || !st) return KMC_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(st, 0, sizeof(*st));
+  st->jobs_done = s->done;
+  st->jobs_queued = s->queue.size();
+  st->batches = s->n_batches;
+  st->max_batch_jobs = s->max_batch_jobs;
+  st->max_inflight_jobs = s->max_inflight_jobs;
+  st->p50_ms = percentile(s->lat_ms, 0.50);
+  st->p99_ms = percentile(s->lat_ms, 0.99);
+  double sum = 0;
+  for (double v : s->lat_ms) sum += v;
+  st->mean_ms = s->lat_ms.empty() ? 0 : sum / (double)s->lat_ms.size();
+  st->wall_s = s->t_last > s->t_first ? s->t_last - s->t_first : 0;
+  st->error = s->error;
+  return KMC_OK;
+}
+
+void kmc_server_close(kmc_server *s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (std::thread &t : s->workers) t.join();
+  for (kmc_batch *b : s->batches) kmc_batch_close(b);
+  delete s;
+}
+
+}  // extern "C"

@@ -78,6 +78,26 @@ class kmc_batch_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class kmc_server_cfg(ctypes.Structure):
+    _fields_ = [
+        ("base", kmc_params), ("batch_bases", ctypes.c_uint64), ("batch_reads", ctypes.c_uint64),
+        ("batch_sets", ctypes.c_uint32), ("n_workers", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+        ("batch_flags", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+    ]
+
+
+class kmc_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("jobs_done", ctypes.c_uint64), ("jobs_queued", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+        ("max_batch_jobs", ctypes.c_uint64), ("max_inflight_jobs", ctypes.c_uint64),
+        ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+        ("wall_s", ctypes.c_double), ("error", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved0"}
+
+
 KMC_BATCH_AUTOTUNE = 1
 KMC_BATCH_NO_GRAPH = 2
 
@@ -119,6 +139,14 @@ SIGNATURES = [
                                         _u64p]),
     ("kmc_batch_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_batch_stats)]),
     ("kmc_batch_close", None, [_vp]),
+    ("kmc_server_open", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(kmc_server_cfg)]),
+    ("kmc_server_submit", ctypes.c_int, [_vp, ctypes.c_uint32, _vp, _u64p, ctypes.c_uint64, _u64p]),
+    ("kmc_server_wait", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double]),
+    ("kmc_server_result", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                         _u64p, ctypes.POINTER(ctypes.c_double)]),
+    ("kmc_server_release", ctypes.c_int, [_vp, ctypes.c_uint64]),
+    ("kmc_server_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_server_stats)]),
+    ("kmc_server_close", None, [_vp]),
     ("kmc_count_small_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64,
                                                _vp, _vp]),
@@ -326,6 +354,61 @@ def kmc_batch_stats_get(b) -> dict:
 def kmc_batch_close(b):
     if b:
         load().kmc_batch_close(b)
+
+
+def kmc_server_open(base: kmc_params, batch_bases=0, batch_reads=0, batch_sets=0, n_workers=0,
+                    mem_budget=0, batch_flags=0) -> int:
+    c = kmc_server_cfg()
+    c.base = base
+    c.batch_bases, c.batch_reads, c.batch_sets = batch_bases, batch_reads, batch_sets
+    c.n_workers, c.mem_budget, c.batch_flags = n_workers, mem_budget, batch_flags
+    h = _vp()
+    _check(load().kmc_server_open(ctypes.byref(h), ctypes.byref(c)), "kmc_server_open")
+    return h.value
+
+
+def kmc_server_submit(s, k: int, bases: np.ndarray, offsets: np.ndarray) -> int:
+    bases = np.ascontiguousarray(bases, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    jid = ctypes.c_uint64()
+    _check(load().kmc_server_submit(s, k, bases.ctypes.data if bases.size else None,
+                                    _ptr(offsets, ctypes.c_uint64), offsets.size - 1, ctypes.byref(jid)),
+           "kmc_server_submit")
+    return jid.value
+
+
+def kmc_server_wait(s, job_id: int, timeout_s: float = -1.0) -> bool:
+    rc = load().kmc_server_wait(s, job_id, timeout_s)
+    if rc == KMC_EAGAIN:
+        return False
+    _check(rc, "kmc_server_wait")
+    return True
+
+
+def kmc_server_result(s, job_id: int):
+    dk, dc, n, lat = _vp(), _vp(), ctypes.c_uint64(), ctypes.c_double()
+    _check(load().kmc_server_result(s, job_id, ctypes.byref(dk), ctypes.byref(dc), ctypes.byref(n),
+                                    ctypes.byref(lat)), "kmc_server_result")
+    if n.value == 0:
+        return np.zeros((0, 1), np.uint64), np.zeros(0, np.uint32), lat.value
+    kms = np.ctypeslib.as_array(ctypes.cast(dk.value, _u64p), shape=(n.value,)).copy().reshape(-1, 1)
+    cnt = np.ctypeslib.as_array(ctypes.cast(dc.value, _u32p), shape=(n.value,)).copy()
+    return kms, cnt, lat.value
+
+
+def kmc_server_release(s, job_id: int):
+    _check(load().kmc_server_release(s, job_id), "kmc_server_release")
+
+
+def kmc_server_stats_get(s) -> dict:
+    st = kmc_server_stats()
+    _check(load().kmc_server_stats_get(s, ctypes.byref(st)), "kmc_server_stats_get")
+    return st.as_dict()
+
+
+def kmc_server_close(s):
+    if s:
+        load().kmc_server_close(s)
 
 
 # ----------------------------------------------------------- convenience
