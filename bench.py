@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the batched / served comparisons")
+    ap.add_argument("--batch-sets", type=int, default=300)
+    ap.add_argument("--batch-scale", type=float, default=0.02)
+    ap.add_argument("--served-jobs", type=int, default=300)
+    ap.add_argument("--served-rho", type=float, nargs="+", default=[0.8, 2.0],
+                    help="loads relative to the serial plain path's capacity")
     return ap.parse_args()
 
 
@@ -275,6 +281,14 @@ def run_ours(args, rank, local_rank, world):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, k, ci, cx)
+    modes = None
+    if rank == 0 and world == 1 and not args.no_modes:
+        modes = {}
+        for name, fn in (("batched", run_batched), ("served", run_served)):
+            try:
+                modes[name] = fn(args, local_rank)
+            except Exception as e:  # reported, never hides the main line
+                modes[name] = {"error": f"{type(e).__name__}: {e}"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -287,9 +301,134 @@ def run_ours(args, rank, local_rank, world):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "scale": args.scale},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "stages": stages,
-        "cpu_baseline": cpu, "clocks": clk,
+        "cpu_baseline": cpu, "clocks": clk, "modes": modes,
     }
     return out
+
+
+# ------------------------------------------------------------ batched / served
+
+def _mode_sets(n, scale, seed_base=0):
+    """Sets shaped like the batched workload (log-normal read counts with median
+    200 k, genomes 1-20 Mbp, L in {100,150,250}, k in {21,28,31}, 1 % errors, no
+    N), with read counts and genome sizes multiplied by `scale`."""
+    from paper_1407_1507_gb300 import synth
+    out = []
+    for i in range(n):
+        n_reads, genome, L, k = synth.batch_set_params(seed_base + i)
+        nr = max(1, int(n_reads * scale))
+        g = synth.genome_markov3(max(int(genome * scale), L + 1), synth.BASE_SEED + 10_000 + seed_base + i)
+        b, o = synth.reads(g, np.full(nr, L), 0.01, 0.0, synth.BASE_SEED + 20_000 + seed_base + i)
+        out.append((b, o, k, nr * (L - k + 1)))
+    return out
+
+
+def run_batched(args, local_rank):
+    """Batched mode (kmc_batch_run, one graph-replayed launch sequence per
+    sub-batch, autotuned) against the plain loop of one kmc_open / add /
+    count / result per set, both through the public API from host memory."""
+    import torch
+    from paper_1407_1507_gb300 import kmc
+    sets = _mode_sets(args.batch_sets, args.batch_scale)
+    pos = sum(x[3] for x in sets)
+    # plain per-set loop
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    plain = []
+    for b, o, k, _ in sets:
+        with kmc.Counter(k, m=7, n_bins=64, device=local_rank) as c:
+            plain.append(c.add(b, o).count().result())
+    t_plain = time.perf_counter() - t
+    p = kmc.make_params(28, m=7, n_bins=64, device=local_rank)
+    bh = kmc.kmc_batch_open(p, 256 << 20, 2_000_000, 512, kmc.KMC_BATCH_AUTOTUNE)
+    try:
+        kmc.kmc_batch_run(bh, [(x[0], x[1]) for x in sets], [x[2] for x in sets])  # tunes + captures
+        t = time.perf_counter()
+        kmc.kmc_batch_run(bh, [(x[0], x[1]) for x in sets], [x[2] for x in sets])
+        t_batch = time.perf_counter() - t
+        st = kmc.kmc_batch_stats_get(bh)
+        same = all(np.array_equal(kmc.kmc_batch_result(bh, i)[0], plain[i][0]) and
+                   np.array_equal(kmc.kmc_batch_result(bh, i)[1], plain[i][1]) for i in range(len(sets)))
+    finally:
+        kmc.kmc_batch_close(bh)
+    return {"workload": f"{len(sets)} sets shaped like the batched workload, read counts and genomes x{args.batch_scale}",
+            "kmer_positions": pos, "plain_kmers_per_s": pos / t_plain, "batched_kmers_per_s": pos / t_batch,
+            "speedup": t_plain / t_batch, "identical_to_plain": bool(same), "sub_batches": st["n_sub_batches"],
+            "single_path_sets": st["n_single"], "tuning": {"bins_per_set": st["bins_per_set"],
+                                                          "tile_keys": st["tile_keys"],
+                                                          "bucket_keys": st["bucket_keys"]}}
+
+
+def run_served(args, local_rank):
+    """Served mode: Poisson arrivals at load rho (relative to the serial plain
+    path's capacity), continuous batching, p50/p99 latency and aggregate
+    throughput, against serial plain execution of the same arrivals (one job at
+    a time, FIFO; its latencies follow from the measured service times)."""
+    from paper_1407_1507_gb300 import kmc
+    rng = np.random.default_rng(20140715)
+    jobs = _mode_sets(args.served_jobs, args.batch_scale, seed_base=5000)
+    # 5 % large jobs (10 M reads at full scale)
+    for i in range(0, len(jobs), 20):
+        b, o, k, _ = jobs[i]
+        from paper_1407_1507_gb300 import synth
+        L = int(o[1] - o[0]) if o.size > 1 else 150
+        nr = max(1, int(10_000_000 * args.batch_scale))
+        g = synth.genome_markov3(max(int(5_000_000 * args.batch_scale), L + 1), 31337 + i)
+        b2, o2 = synth.reads(g, np.full(nr, L), 0.01, 0.0, 4242 + i)
+        jobs[i] = (b2, o2, k, nr * (L - k + 1))
+    pos = sum(x[3] for x in jobs)
+    # serial plain: service times one job at a time
+    svc = []
+    for b, o, k, _ in jobs:
+        t = time.perf_counter()
+        with kmc.Counter(k, m=7, n_bins=64, device=local_rank) as c:
+            c.add(b, o).count().result()
+        svc.append(time.perf_counter() - t)
+    mean_svc = float(np.mean(svc))
+    out = {"workload": f"{len(jobs)} Poisson requests, sizes and k as the batched sets x{args.batch_scale}, "
+                       "5% large jobs", "kmer_positions": pos,
+           "serial_plain_mean_service_ms": mean_svc * 1e3}
+    for rho in args.served_rho:
+        out[f"rho={rho}"] = _served_run(kmc, jobs, svc, rho, rng, local_rank, pos)
+    return out
+
+
+def _served_run(kmc, jobs, svc, rho, rng, local_rank, pos):
+    lam = rho / float(np.mean(svc))
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
+    done, lat_serial = 0.0, []
+    for a, sv in zip(arrivals, svc):
+        start = max(a, done)
+        done = start + sv
+        lat_serial.append((done - a) * 1e3)
+    serial_wall = done - arrivals[0]
+    s = kmc.kmc_server_open(kmc.make_params(28, m=7, n_bins=64, device=local_rank),
+                            batch_bases=128 << 20, batch_reads=1_000_000, batch_sets=256, n_workers=2,
+                            warm_k=(21, 28, 31))
+    try:
+        st0 = kmc.kmc_server_stats_get(s)
+        t0 = time.perf_counter()
+        ids = []
+        for (b, o, k, _), a in zip(jobs, arrivals - arrivals[0]):
+            d = t0 + a - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids.append(kmc.kmc_server_submit(s, k, b, o))
+        lat = []
+        for jid in ids:
+            kmc.kmc_server_wait(s, jid, 600.0)
+            lat.append(kmc.kmc_server_result(s, jid)[2])
+        wall = time.perf_counter() - t0
+        st = kmc.kmc_server_stats_get(s)
+    finally:
+        kmc.kmc_server_close(s)
+    return {"arrival_rate_per_s": lam,
+            "served_kmers_per_s": pos / wall, "serial_plain_kmers_per_s": pos / serial_wall,
+            "served_p50_ms": float(np.percentile(lat, 50)), "served_p99_ms": float(np.percentile(lat, 99)),
+            "serial_plain_p50_ms": float(np.percentile(lat_serial, 50)),
+            "serial_plain_p99_ms": float(np.percentile(lat_serial, 99)),
+            "batches": st["batches"] - st0["batches"], "max_batch_jobs": st["max_batch_jobs"],
+            "max_inflight_jobs": st["max_inflight_jobs"]}
 
 
 def run_reference(args, rank, world):

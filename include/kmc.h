@@ -295,6 +295,9 @@ typedef struct {
                             64 x batch_bases)                               */
   uint32_t batch_flags;  /* KMC_BATCH_* for the workers' batch handles      */
   uint32_t reserved0;
+  uint64_t warm_k_mask;  /* bit k set (1..32): every worker builds and
+                            captures its engine for k at open, on synthetic
+                            reads, so that first requests do not pay for it */
 } kmc_server_cfg;
 typedef struct {
   uint64_t jobs_done;
@@ -360,6 +363,9 @@ int kmc_count_small_noalloc(const char *d_bases, const uint64_t *d_offsets, uint
  * sharing their sorted bits become common and the regrouping of such runs
  * is exercised (tests); the result is the same, only slower. */
 #define KMC_DEBUG_NARROW_SORT 4u
+/* Computes signatures with the tile-doubling scan kernel instead of the
+ * lane-block one (both give the same super k-mers; for cross-checks). */
+#define KMC_DEBUG_SIG_TILE 8u
 
 #ifdef __cplusplus
 }

@@ -201,7 +201,8 @@ int validate(const kmc_params *p) {
   if (p->cutoff_min > p->cutoff_max) return KMC_EINVAL;
   if (p->canonical != 1) return KMC_EINVAL;
   if (p->reserved0 || p->reserved[0] || p->reserved[1]) return KMC_EINVAL;
-  if (p->debug_flags & ~(KMC_DEBUG_KEEP_SUPERKMERS | KMC_DEBUG_KEEP_KEYS | KMC_DEBUG_NARROW_SORT))
+  if (p->debug_flags & ~(KMC_DEBUG_KEEP_SUPERKMERS | KMC_DEBUG_KEEP_KEYS | KMC_DEBUG_NARROW_SORT |
+                         KMC_DEBUG_SIG_TILE))
     return KMC_EINVAL;
   return KMC_OK;
 }

@@ -236,8 +236,7 @@ struct BatchEngine {
       return KMC_ENOMEM;
     }
     // kernel attributes and occupancies are set here, outside any capture
-    KMC_CUDA_TRY(cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(SigSmem)));
+    KMC_CUDA_TRY(sig_prepare());
     KMC_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sizeof(ScatSmem)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_scatter_kernel<uint64_t>,
@@ -430,8 +429,7 @@ int BatchEngine::sequence() {
   a.set_starts = as<uint64_t>(set_starts);
   a.n_slots = max_sets;
   a.bins_per_slot = tune.bins;
-  sig_kernel<<<(unsigned)((n_stream_max + SIG_TPOS - 1) / SIG_TPOS), SIG_THREADS, sizeof(SigSmem), st>>>(a);
-  KMC_COUNT_LAUNCH();
+  if (sig_launch(a, n_stream_max, false, st)) KMC_COUNT_LAUNCH();
   // a3: bins
   KMC_CUDA_TRY(device_excl_scan_u64(reinterpret_cast<uint64_t *>(h_rec), as<uint64_t>(rec_base), B_total,
                                     as<uint64_t>(scan_tmp), st));

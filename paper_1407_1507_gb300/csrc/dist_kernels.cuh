@@ -12,6 +12,8 @@
 // only the device knows (stream length, number of super k-mers) can be read
 // from device memory (`dyn`), so a batch runs without host synchronisation.
 #pragma once
+#include <atomic>
+
 #include "common.cuh"
 #include "sortlib.cuh"
 
@@ -355,6 +357,292 @@ __global__ void __launch_bounds__(SIG_THREADS) sig_kernel(SigArgs a) {
       }
     }
   }
+}
+
+// ----------------------------------------------- a2, lane-block version
+// Same result as sig_kernel, organised for fewer instructions per position.
+// Each of the 256 lanes of a CTA owns a block of w = k-m+1 consecutive
+// positions.  A lane rolls its m-mer values (canonical, rule-filtered) over
+// its block and stores them with their running prefix minima in its own
+// shared-memory row; the minimum over the window [p, p+w-1] is then the
+// smaller of the suffix minimum of p's block (from p) and the prefix minimum
+// of the next block (to p+w-1): van Herk / Gil-Werman with block size w.
+// Lane 255 only lends its prefix minima, so a CTA covers 255*w positions,
+// starting one position before the k-mer starts it owns and extending
+// kSuperkmerCap past them (a super k-mer never spans more).
+
+constexpr int SIG2_LANES = 256;
+constexpr int SIG2_MAXW = 64;
+constexpr int SIG2_MWORDS = (SIG2_LANES * SIG2_MAXW + 256) / 64 + 4;  // mask words staged
+constexpr int SIG2_PWORDS = 2 * SIG2_MWORDS;                            // packed words staged
+static_assert((kSuperkmerCap & (kSuperkmerCap - 1)) == 0, "cut test uses a mask");
+
+__host__ __device__ inline int sig2_own(int k, int m) {
+  const int w = k - m + 1;
+  return (SIG2_LANES - 1) * w - 1 - kSuperkmerCap;  // owned k-mer start positions per CTA
+}
+__host__ __device__ inline int sig2_stride(int k, int m) {
+  return (k - m + 1) | 1;  // odd row stride: lanes touching the same column hit distinct banks
+}
+__host__ __device__ inline int sig2_hist_bins(uint32_t n_bins) {
+  return n_bins <= (uint32_t)SIG_SMEM_BINS ? (int)n_bins : 0;
+}
+inline size_t sig2_smem_bytes(int k, int m, uint32_t n_bins) {
+  return (size_t)SIG2_PWORDS * 8 + 4 * (size_t)SIG2_MWORDS * 8 + (size_t)SIG2_LANES * 8 +
+         2 * (size_t)SIG2_LANES * sig2_stride(k, m) * 4 + 3 * (size_t)sig2_hist_bins(n_bins) * 4;
+}
+// The lane-block form pays off once a block holds several positions.
+inline bool sig2_applies(int k, int m) { return k - m + 1 >= 8 && k - m + 1 <= SIG2_MAXW; }
+
+__global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = threadIdx.x;
+  const int k = a.k, m = a.m, w = k - m + 1;
+  const int own = sig2_own(k, m), stride = sig2_stride(k, m);
+  const int64_t T0 = (int64_t)blockIdx.x * own;        // first owned start
+  if (a.n_stream_dyn && (unsigned long long)T0 >= *a.n_stream_dyn) return;
+  const int64_t B0 = T0 - 1;                           // first position of lane 0's block
+  const uint32_t SENT = 1u << (2 * m);
+  const int hb = sig2_hist_bins(a.n_bins);
+  const bool small_bins = hb > 0;
+  // shared memory carve-up
+  uint64_t *pk = reinterpret_cast<uint64_t *>(smem_raw);
+  uint64_t *iv = pk + SIG2_PWORDS;                      // invalid bases
+  uint64_t *sm = iv + SIG2_MWORDS;                      // read starts
+  uint64_t *cm = sm + SIG2_MWORDS;                      // invalid base or read start
+  int64_t *lastw = reinterpret_cast<int64_t *>(cm + SIG2_MWORDS);
+  int64_t *fbrk = lastw + SIG2_MWORDS;                  // first break of each lane's block
+  uint32_t *V = reinterpret_cast<uint32_t *>(fbrk + SIG2_LANES);   // values, then signatures
+  uint32_t *P = V + SIG2_LANES * stride;                           // prefix minima
+  uint32_t *h_rec = P + SIG2_LANES * stride;
+  uint32_t *h_words = h_rec + hb;
+  uint32_t *h_kmers = h_words + hb;
+  __shared__ uint32_t ws[SIG2_LANES / 32 + 1];
+  __shared__ int64_t rs0;
+  __shared__ unsigned long long out_base;
+  // stage packed codes and masks from position B0 (rounded down to a word)
+  const int64_t pw0 = B0 >= 0 ? B0 / 32 : -1;
+  const int64_t LB = pw0 * 32;
+  const int64_t mw0 = B0 >= 0 ? B0 / 64 : -1;
+  const int64_t LBm = mw0 * 64;
+  for (int i = L; i < SIG2_PWORDS; i += SIG2_LANES) {
+    const int64_t gi = pw0 + i;
+    pk[i] = (gi >= 0 && (uint64_t)gi < a.n_pwords) ? a.packed[gi] : 0ull;
+  }
+  for (int i = L; i < SIG2_MWORDS; i += SIG2_LANES) {
+    const int64_t gi = mw0 + i;
+    const bool in = gi >= 0 && (uint64_t)gi < a.n_mwords;
+    const uint64_t x = in ? a.inval[gi] : ~0ull, y = in ? a.smask[gi] : 0ull;
+    iv[i] = x;
+    sm[i] = y;
+    cm[i] = x | y;
+  }
+  if (small_bins && a.list)
+    for (int i = L; i < hb; i += SIG2_LANES) h_rec[i] = h_words[i] = h_kmers[i] = 0;
+  if (L == 0) {
+    // start of the read holding position max(LBm, 0)
+    uint64_t lo = a.r0, hi = a.r1;
+    if (a.n_reads_dyn && *a.n_reads_dyn < hi) hi = *a.n_reads_dyn;
+    int64_t rs = 0;
+    const int64_t q = LBm > 0 ? LBm : 0;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) / 2;
+      const int64_t sp = (int64_t)(a.offsets[mid] - a.byte_start) + a.mis;
+      if (sp <= q) { rs = sp; lo = mid + 1; } else hi = mid;
+    }
+    rs0 = rs;
+  }
+  __syncthreads();
+  if (L < 32) {
+    // last read start strictly before each staged mask word (prefix max)
+    int64_t carry = rs0;
+    for (int base = 0; base < SIG2_MWORDS; base += 32) {
+      const int i = base + L;
+      int64_t here = -1;
+      if (i < SIG2_MWORDS && sm[i]) here = LBm + (int64_t)i * 64 + 64 - __ffsll((long long)sm[i]);
+      int64_t v = here;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o = __shfl_up_sync(FULL, v, d);
+        if (L >= d && o > v) v = o;
+      }
+      int64_t excl = __shfl_up_sync(FULL, v, 1);
+      if (L == 0) excl = -1;
+      if (i < SIG2_MWORDS) lastw[i] = excl > carry ? excl : carry;
+      const int64_t tot = __shfl_sync(FULL, v, 31);
+      if (tot > carry) carry = tot;
+    }
+  }
+  // phase 1: m-mer values of the lane's block and their prefix minima
+  const int64_t p0 = B0 + (int64_t)L * w;               // >= B0 >= LB, LBm
+  {
+    const uint32_t mmask = SENT - 1u;
+    uint32_t fw = 0, rc = 0;
+    uint64_t bit = (uint64_t)(2 * (p0 - LB));
+    for (int q = 0; q < m - 1; ++q, bit += 2) {
+      const uint32_t c = (uint32_t)get_bits(pk, bit, 2);
+      fw = ((fw << 2) | c) & mmask;
+      rc = (rc >> 2) | ((3u - c) << (2 * m - 2));
+    }
+    uint32_t pm = 0xFFFFFFFFu;
+    for (int j = 0; j < w; ++j, bit += 2) {
+      const uint32_t c = (uint32_t)get_bits(pk, bit, 2);
+      fw = ((fw << 2) | c) & mmask;
+      rc = (rc >> 2) | ((3u - c) << (2 * m - 2));
+      const uint32_t cn = fw < rc ? fw : rc;                 // canonical m-mer (Sect. 2.1)
+      const uint32_t v = mmer_allowed(cn, m) ? cn : SENT;     // Sect. 2.2 filter
+      V[L * stride + j] = v;
+      pm = v < pm ? v : pm;
+      P[L * stride + j] = pm;
+    }
+  }
+  __syncthreads();
+  // phase 2: window minima = signatures (lane 255 only lends prefix minima)
+  if (L < SIG2_LANES - 1) {
+    uint32_t sfx = 0xFFFFFFFFu;
+    for (int j = w - 1; j >= 0; --j) {
+      const uint32_t v = V[L * stride + j];
+      sfx = v < sfx ? v : sfx;
+      const uint32_t nx = j > 0 ? P[(L + 1) * stride + j - 1] : 0xFFFFFFFFu;
+      V[L * stride + j] = sfx < nx ? sfx : nx;
+    }
+  }
+  __syncthreads();
+  // phase 3: validity, cut rule, breaks and owned starts of the lane's block
+  const int64_t own_end = T0 + own;
+  uint64_t brk_mask = 0, start_mask = 0;
+  if (L < SIG2_LANES - 1) {
+    // a k-mer at pos is valid when its k bases are bases and no read starts
+    // inside it (after pos)
+    auto valid_at = [&](uint64_t lp) -> bool {
+      if ((iv[lp >> 6] >> (63 - (lp & 63))) & 1ull) return false;
+      return k == 1 || get_bits(cm, lp + 1, k - 1) == 0ull;
+    };
+    // lane 0's first position precedes the owned range: no start flag needed
+    bool pv = false;
+    uint32_t psig = 0;
+    const uint64_t lp0 = (uint64_t)(p0 - LBm);
+    if (L > 0) {
+      pv = valid_at(lp0 - 1);
+      psig = V[(L - 1) * stride + (w - 1)];
+    }
+    // last read start strictly before p0
+    int64_t rs;
+    {
+      const int wi = (int)(lp0 >> 6);
+      const unsigned o = (unsigned)(lp0 & 63);
+      const uint64_t x = o ? (sm[wi] & (~0ull << (64 - o))) : 0ull;
+      rs = x ? LBm + (int64_t)wi * 64 + 64 - __ffsll((long long)x) : lastw[wi];
+    }
+    for (int j = 0; j < w; ++j) {
+      const int64_t pos = p0 + j;
+      const uint64_t lp = lp0 + j;
+      if ((sm[lp >> 6] >> (63 - (lp & 63))) & 1ull) rs = pos;
+      const bool v = pos >= 0 && valid_at(lp);
+      const uint32_t sg = V[L * stride + j];
+      const bool cut = v && (((uint32_t)(pos - rs) & (kSuperkmerCap - 1)) == 0);
+      const bool st = v && (!pv || sg != psig || cut);
+      if (!v || st) brk_mask |= 1ull << j;
+      if (st && pos >= T0 && pos < own_end) start_mask |= 1ull << j;
+      pv = v;
+      psig = sg;
+    }
+  }
+  fbrk[L] = brk_mask ? p0 + (__ffsll((long long)brk_mask) - 1) : INT64_MAX;
+  __syncthreads();
+  // phase 4: emit the owned super k-mers (each ends at the next break)
+  const uint32_t ns = (uint32_t)__popcll(start_mask);
+  uint32_t nst;
+  uint32_t si = block_excl_scan<uint32_t, SIG2_LANES>(ns, ws, &nst);
+  if (a.list) {
+    if (L == 0) out_base = nst ? atomicAdd(a.n_list, (unsigned long long)nst) : 0ull;
+    __syncthreads();
+    if (out_base + nst > a.list_cap) {
+      if (L == 0) atomicOr(a.err, ERR_CAPACITY);
+      return;
+    }
+  }
+  uint64_t bits = start_mask;
+  while (bits) {
+    const int j = __ffsll((long long)bits) - 1;
+    bits &= bits - 1;
+    const int64_t pos = p0 + j;
+    // next break after j: in this block, else the first break of a later block
+    const uint64_t after = j < 63 ? (brk_mask >> (j + 1)) << (j + 1) : 0ull;
+    int64_t end;
+    if (after) {
+      end = p0 + (__ffsll((long long)after) - 1);
+    } else {
+      end = B0 + (int64_t)(SIG2_LANES - 1) * w;  // end of the covered positions
+      for (int l2 = L + 1; l2 < SIG2_LANES - 1; ++l2) {
+        const int64_t f = fbrk[l2];
+        if (f != INT64_MAX) { end = f; break; }
+      }
+    }
+    const uint32_t n = (uint32_t)(end - pos);
+    const uint32_t g = V[L * stride + j];
+    if (!a.list) {  // sample mode: signature weights
+      atomicAdd(&a.sig_weight[g], (unsigned long long)n);
+      continue;
+    }
+    a.list[out_base + si] = ((uint64_t)pos << 32) | ((uint64_t)(n - 1) << 25) | g;
+    ++si;
+    const uint32_t bin = slot_of(a.set_starts, a.n_slots, (uint64_t)pos) * a.bins_per_slot + a.map[g];
+    const uint32_t nw = (2 * (n + k - 1) + 63) / 64;
+    if (small_bins) {
+      atomicAdd(&h_rec[bin], 1u);
+      atomicAdd(&h_words[bin], nw);
+      atomicAdd(&h_kmers[bin], n);
+    } else {
+      atomicAdd(&a.bin_rec[bin], 1ull);
+      atomicAdd(&a.bin_words[bin], (unsigned long long)nw);
+      atomicAdd(&a.bin_kmers[bin], (unsigned long long)n);
+    }
+  }
+  if (small_bins && a.list) {
+    __syncthreads();
+    for (int i = L; i < hb; i += SIG2_LANES) {
+      if (h_rec[i]) {
+        atomicAdd(&a.bin_rec[i], (unsigned long long)h_rec[i]);
+        atomicAdd(&a.bin_words[i], (unsigned long long)h_words[i]);
+        atomicAdd(&a.bin_kmers[i], (unsigned long long)h_kmers[i]);
+      }
+    }
+  }
+}
+
+// Raises the shared-memory limits of both signature kernels (once per
+// device; must not run inside a graph capture).
+inline cudaError_t sig_prepare() {
+  static std::atomic<uint8_t> done[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && done[dev].load()) return cudaSuccess;
+  e = cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SigSmem));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(sig2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sig2_smem_bytes(SIG2_MAXW, 1, SIG_SMEM_BINS));
+  if (e != cudaSuccess) return e;
+  if (dev < 64) done[dev].store(1);
+  return cudaSuccess;
+}
+
+// Launches the signature scan over stream positions [0, n_stream) (the
+// lane-block kernel unless `tile` asks for the tile-doubling one or the
+// window is outside its range).  Returns the launches made (0 or 1).
+inline int sig_launch(const SigArgs &a, uint64_t n_stream, bool tile, cudaStream_t st) {
+  if (!tile && sig2_applies(a.k, a.m)) {
+    const uint64_t own = (uint64_t)sig2_own(a.k, a.m);
+    const uint64_t g = (n_stream + own - 1) / own;
+    if (g == 0) return 0;
+    sig2_kernel<<<(unsigned)g, SIG2_LANES, sig2_smem_bytes(a.k, a.m, a.n_bins), st>>>(a);
+    return 1;
+  }
+  const uint64_t g = (n_stream + SIG_TPOS - 1) / SIG_TPOS;
+  if (g == 0) return 0;
+  sig_kernel<<<(unsigned)g, SIG_THREADS, sizeof(SigSmem), st>>>(a);
+  return 1;
 }
 
 // ------------------------------------------------------------------ a3

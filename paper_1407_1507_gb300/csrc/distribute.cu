@@ -84,16 +84,10 @@ SigArgs sig_args(Handle &h, const StreamInfo &si, const uint64_t *d_offsets, uin
 }
 
 int launch_sig(Handle &h, const SigArgs &a, uint64_t n_stream, int stage) {
-  const uint64_t n_tiles = (n_stream + SIG_TPOS - 1) / SIG_TPOS;
-  static bool attr_set = false;
-  if (!attr_set) {
-    KMC_CUDA_TRY(cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(SigSmem)));
-    attr_set = true;
-  }
-  if (n_tiles == 0) return KMC_OK;
+  KMC_CUDA_TRY(sig_prepare());
+  if (n_stream == 0) return KMC_OK;
   StageScope sc(h, stage);
-  sig_kernel<<<(unsigned)n_tiles, SIG_THREADS, sizeof(SigSmem), h.st>>>(a); KMC_COUNT_LAUNCH();
+  if (sig_launch(a, n_stream, (h.p.debug_flags & KMC_DEBUG_SIG_TILE) != 0, h.st)) KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
   return KMC_OK;
 }

@@ -68,6 +68,7 @@ struct kmc_server {
   uint64_t done = 0, n_batches = 0, max_batch_jobs = 0, max_inflight_jobs = 0;
   double t_first = 0, t_last = 0;
   int error = 0;
+  uint32_t ready = 0;  // workers done warming up
 };
 
 namespace {
@@ -82,9 +83,40 @@ bool fits(const kmc_server &s, const std::vector<Job *> &take, uint64_t nb, uint
   return nb + jb + 64 <= c.batch_bases && nr + j.n_reads + 1 <= c.batch_reads;
 }
 
+// Builds (and captures) the worker's engine of every k in warm_k_mask by
+// counting a small synthetic read set with it.
+int warm_up(kmc_batch *b, uint64_t mask) {
+  std::vector<char> bases(4000 * 150);
+  uint64_t x = 0x2545F4914F6CDD1Dull;
+  for (char &c : bases) {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    c = "ACGT"[x & 3];
+  }
+  std::vector<uint64_t> offs(4001);
+  for (int i = 0; i <= 4000; ++i) offs[i] = (uint64_t)i * 150;
+  for (uint32_t k = 1; k <= 32; ++k) {
+    if (!((mask >> k) & 1)) continue;
+    const char *bp = bases.data();
+    const uint64_t *op = offs.data();
+    const uint64_t nr = 4000;
+    int rc = kmc_batch_run(b, 1, &bp, &op, &nr, &k);
+    if (rc) return rc;
+  }
+  return KMC_OK;
+}
+
 void worker(kmc_server *s, int w) {
   kmc_batch *b = s->batches[w];
   cudaSetDevice(s->cfg.base.device);
+  const int wrc = warm_up(b, s->cfg.warm_k_mask);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (wrc) s->error = wrc;
+    s->ready += 1;
+  }
+  s->cv_done.notify_all();
   for (;;) {
     std::vector<Job *> take;
     uint64_t fp = 0;
@@ -212,6 +244,16 @@ int kmc_server_open(kmc_server **out, const kmc_server_cfg *cfg) {
     s->batches.push_back(b);
   }
   for (uint32_t w = 0; w < c.n_workers; ++w) s->workers.emplace_back(worker, s, (int)w);
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] { return s->ready == c.n_workers; });
+    if (s->error) {
+      const int rc = s->error;
+      lk.unlock();
+      kmc_server_close(s);
+      return rc;
+    }
+  }
   *out = s;
   return KMC_OK;
 }

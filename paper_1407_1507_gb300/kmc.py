@@ -29,6 +29,7 @@ KMC_AUTO = 0xFFFFFFFF
 KMC_DEBUG_KEEP_SUPERKMERS = 1
 KMC_DEBUG_KEEP_KEYS = 2
 KMC_DEBUG_NARROW_SORT = 4
+KMC_DEBUG_SIG_TILE = 8
 
 
 class kmc_params(ctypes.Structure):
@@ -83,6 +84,7 @@ class kmc_server_cfg(ctypes.Structure):
         ("base", kmc_params), ("batch_bases", ctypes.c_uint64), ("batch_reads", ctypes.c_uint64),
         ("batch_sets", ctypes.c_uint32), ("n_workers", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
         ("batch_flags", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+        ("warm_k_mask", ctypes.c_uint64),
     ]
 
 
@@ -357,11 +359,12 @@ def kmc_batch_close(b):
 
 
 def kmc_server_open(base: kmc_params, batch_bases=0, batch_reads=0, batch_sets=0, n_workers=0,
-                    mem_budget=0, batch_flags=0) -> int:
+                    mem_budget=0, batch_flags=0, warm_k=()) -> int:
     c = kmc_server_cfg()
     c.base = base
     c.batch_bases, c.batch_reads, c.batch_sets = batch_bases, batch_reads, batch_sets
     c.n_workers, c.mem_budget, c.batch_flags = n_workers, mem_budget, batch_flags
+    c.warm_k_mask = sum(1 << k for k in warm_k)
     h = _vp()
     _check(load().kmc_server_open(ctypes.byref(h), ctypes.byref(c)), "kmc_server_open")
     return h.value

@@ -51,7 +51,9 @@ def test_random_small_inputs(seed):
                        p_n=rng.choice([0.0, 0.01, 0.05]), alphabet=rng.choice(["ACGT", "ACGT", "AC"]))
     ci = rng.choice([1, 2])
     b, o = oracle.as_reads(reads)
-    assert_same(gpu_count(b, o, k, m=m, n_bins=B, cutoff_min=ci), oracle_count(b, o, k, ci))
+    want = oracle_count(b, o, k, ci)
+    for flags in (0, kmc.KMC_DEBUG_SIG_TILE):
+        assert_same(gpu_count(b, o, k, m=m, n_bins=B, cutoff_min=ci, debug_flags=flags), want)
 
 
 def test_tiny_workload_full_size():
@@ -167,10 +169,14 @@ def test_device_input_equals_host_input():
     assert_same(got, want)
 
 
-def test_superkmers_match_oracle_split():
+@pytest.mark.parametrize("k,m,flags", [(28, 7, 0), (28, 7, 8), (21, 9, 0), (64, 7, 0), (64, 7, 8),
+                                        (12, 7, 0), (40, 11, 0), (32, 5, 0)])
+def test_superkmers_match_oracle_split(k, m, flags):
+    # flags 8 = KMC_DEBUG_SIG_TILE (tile-doubling signature kernel); k=12, m=7
+    # (window of 6 m-mers) takes that kernel in any case
     w = synth.mid(scale=0.0005)
-    k, m = 28, 7
-    with kmc.Counter(k, m=m, n_bins=64, debug_flags=kmc.KMC_DEBUG_KEEP_SUPERKMERS) as c:
+    flags |= kmc.KMC_DEBUG_KEEP_SUPERKMERS
+    with kmc.Counter(k, m=m, n_bins=64, debug_flags=flags) as c:
         c.add(w.bases, w.offsets)
         rd, ps, nk, sg = kmc.kmc_debug_superkmers(c.h)
     got = sorted(zip(rd.tolist(), ps.tolist(), nk.tolist(), sg.tolist()))
