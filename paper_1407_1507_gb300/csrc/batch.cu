@@ -218,7 +218,7 @@ struct BatchEngine {
         E(pieces, 64) || E(hist, NB_max * 4) || E(bucket_base, (NB_max + 1) * 8) ||
         E(flags, NB_max * 4) || E(fscan, (NB_max + 1) * 8) || E(tfirst, NB_max * 4 + 16) ||
         E(scan_tmp, scan_tmp_words(std::max<uint64_t>(NB_max, std::max<uint64_t>(B_total, ond))) * 8) ||
-        E(keys, list_cap * 8) || E(sv_keys, sv_cap * 8) || E(sv_counts, sv_cap * 4) ||
+        E(keys, (list_cap + 2) * 8) || E(sv_keys, sv_cap * 8) || E(sv_counts, sv_cap * 4) ||
         E(sv_slots, sv_cap * 4) || E(big_list, (list_cap / (tile + 1) + 2) * 4) ||
         E(big_scratch, list_cap * 8) || E(counters, 128) || E(okeys, sv_cap * ok) ||
         E(okeys2, sv_cap * ok) || E(ovals2, sv_cap * 4) || E(o_hist, ond * 4) ||
@@ -257,14 +257,15 @@ struct BatchEngine {
   int occ_count = 1, occ_order = 1;
   template <int IPT>
   int prepare_count() {
-    using SM = TileCountSmem<uint64_t, B_THREADS, IPT>;
+    constexpr int GIPT = B_THREADS * IPT / GRP_THREADS;
+    using GSM = TileGroupSmem<uint64_t, GRP_THREADS, GIPT>;
     using BSM = BigSmem<uint64_t, NoVal, B_THREADS, B_BIG_IPT>;
-    KMC_CUDA_TRY(cudaFuncSetAttribute(tile_count_kernel<uint64_t, B_THREADS, IPT>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM)));
+    KMC_CUDA_TRY(cudaFuncSetAttribute(tile_group_kernel<uint64_t, GRP_THREADS, GIPT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GSM)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(big_count_kernel<uint64_t, B_THREADS, B_BIG_IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BSM)));
     KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ_count, tile_count_kernel<uint64_t, B_THREADS, IPT>, B_THREADS, sizeof(SM)));
+        &occ_count, tile_group_kernel<uint64_t, GRP_THREADS, GIPT>, GRP_THREADS, sizeof(GSM)));
     return KMC_OK;
   }
   template <typename KO>
@@ -290,7 +291,8 @@ struct BatchEngine {
 template <int IPT>
 int BatchEngine::count_stage(const TilePlan &plan, const Mixer<uint64_t> &mixer) {
   using K = uint64_t;
-  using SM = TileCountSmem<K, B_THREADS, IPT>;
+  constexpr int GIPT = B_THREADS * IPT / GRP_THREADS;
+  using GSM = TileGroupSmem<K, GRP_THREADS, GIPT>;
   using BSM = BigSmem<K, NoVal, B_THREADS, B_BIG_IPT>;
   auto *c32 = as<uint32_t>(counters);
   auto *c64 = reinterpret_cast<unsigned long long *>(c32 + 4);
@@ -309,9 +311,10 @@ int BatchEngine::count_stage(const TilePlan &plan, const Mixer<uint64_t> &mixer)
   out.bins_per_slot = tune.bins;
   const int occ = occ_count;
   const uint32_t big_cap = (uint32_t)(list_cap / (256ull * IPT + 1) + 2);
-  tile_count_kernel<K, B_THREADS, IPT><<<(unsigned)std::max(1, occ) * sm_count, B_THREADS, sizeof(SM), st>>>(
+  tile_group_kernel<K, GRP_THREADS, GIPT><<<(unsigned)std::max(1, occ) * sm_count, GRP_THREADS, sizeof(GSM),
+                                            st>>>(
       as<K>(keys), plan, c32 + 0, out, as<uint32_t>(big_list), c32 + 1, c64 + 2, big_cap,
-      as<uint32_t>(err), (K *)nullptr);
+      as<uint32_t>(err));
   KMC_COUNT_LAUNCH();
   big_count_kernel<K, B_THREADS, B_BIG_IPT><<<sm_count, B_THREADS, sizeof(BSM), st>>>(
       as<K>(keys), plan, as<uint32_t>(big_list), c32 + 1, as<K>(big_scratch), c64 + 3, out,

@@ -68,21 +68,36 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
   out.sort_bits = (h.p.debug_flags & KMC_DEBUG_NARROW_SORT) ? 8 : kCountSortBits;
   out.slots = nullptr;
   out.bins_per_slot = 1;
+  // tiles are grouped (one radix step + grouping by value) unless the sorted
+  // keys are asked for or the narrow-sort check is on
+  constexpr int GIPT = TILE / GRP_THREADS;
+  using GSM = TileGroupSmem<K, GRP_THREADS, GIPT>;
+  const bool grouped = !sorted_out && out.sort_bits == kCountSortBits;
   static bool attr = false;
   if (!attr) {
     KMC_CUDA_TRY(cudaFuncSetAttribute(tile_count_kernel<K, CNT_THREADS, IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM)));
+    KMC_CUDA_TRY(cudaFuncSetAttribute(tile_group_kernel<K, GRP_THREADS, GIPT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GSM)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(big_count_kernel<K, CNT_THREADS, BIG_IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BSM)));
     attr = true;
   }
   int occ = 0;
-  KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, tile_count_kernel<K, CNT_THREADS, IPT>, CNT_THREADS, sizeof(SM)));
-  const unsigned grid = (unsigned)std::max(1, occ) * (unsigned)h.sm_count;
-  {
+  if (grouped) {
+    KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, tile_group_kernel<K, GRP_THREADS, GIPT>, GRP_THREADS, sizeof(GSM)));
     StageScope sc(h, KMC_STAGE_TILE_SORT);
-    tile_count_kernel<K, CNT_THREADS, IPT><<<grid, CNT_THREADS, sizeof(SM), h.st>>>(
+    tile_group_kernel<K, GRP_THREADS, GIPT><<<(unsigned)std::max(1, occ) * h.sm_count, GRP_THREADS,
+                                              sizeof(GSM), h.st>>>(
+        keys, plan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
+        as<uint32_t>(h.err)); KMC_COUNT_LAUNCH();
+  } else {
+    KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, tile_count_kernel<K, CNT_THREADS, IPT>, CNT_THREADS, sizeof(SM)));
+    StageScope sc(h, KMC_STAGE_TILE_SORT);
+    tile_count_kernel<K, CNT_THREADS, IPT><<<(unsigned)std::max(1, occ) * h.sm_count, CNT_THREADS,
+                                             sizeof(SM), h.st>>>(
         keys, plan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
         as<uint32_t>(h.err), sorted_out); KMC_COUNT_LAUNCH();
   }
@@ -283,7 +298,7 @@ int sort_phase_x0(Handle &h) {
   }
   if (rc) return rc;
   KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));  // hist becomes the per-bucket cursor
-  if (dev_ensure(ss.keys, (n_keys + 1) * sizeof(K), h.st)) return KMC_ENOMEM;
+  if (dev_ensure(ss.keys, (n_keys + 2) * sizeof(K), h.st)) return KMC_ENOMEM;  // 16 B slack
   K *keys = as<K>(ss.keys);
   if (meta.n_chunks) {
     static bool attr = false;
@@ -374,7 +389,7 @@ int sort_phase_kx(Handle &h, int x) {
   KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));
   KMC_CUDA_TRY(cudaStreamSynchronize(h.st));
   h.stats.n_sorted_keys = n_keys1;
-  if (dev_ensure(ss.keys, (n_keys1 + 1) * sizeof(K1), h.st)) return KMC_ENOMEM;
+  if (dev_ensure(ss.keys, (n_keys1 + 2) * sizeof(K1), h.st)) return KMC_ENOMEM;  // 16 B slack
   K1 *keys = as<K1>(ss.keys);
   if (meta.n_chunks) {
     StageScope sc(h, KMC_STAGE_KX_SCATTER);

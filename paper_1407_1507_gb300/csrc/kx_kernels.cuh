@@ -15,6 +15,7 @@ constexpr int CNT_THREADS = 256;
 constexpr int CNT_IPT64 = 16;   // tile = 4096 64-bit keys
 constexpr int CNT_IPT128 = 8;   // tile = 2048 128-bit keys
 constexpr int BIG_IPT = 16;
+constexpr int GRP_THREADS = 512;  // tile_group_kernel (same tile sizes as the sort kernels)
 
 struct PieceDesc {
   const uint64_t *index;

@@ -490,6 +490,258 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
   }
 }
 
+// ----------------------------------------------------- grouping count tiles
+// Count mode without a full sort.  Counting needs equal keys side by side,
+// not the keys in order: the survivors are put in k-mer order afterwards
+// anyway, and the keys of a tile are mixed.  So a tile takes one more radix
+// partition step, on the low kGroupBits bits of its keys (one shared-memory
+// atomic per key gives both the digit histogram and the key's rank in its
+// digit).  A digit bucket then mostly holds copies of one key (at 60x
+// coverage a genomic k-mer has dozens), sometimes a few values.  The values
+// of a bucket are separated in rounds: each round every unsettled key
+// compares itself with the bucket's representative (first the bucket's
+// first key, then any unsettled key); the equal ones settle, and the rest
+// count themselves, so the representative's group size is the drop of that
+// count.  Rounds = most values in one bucket; heavy keys cost no serial work.
+// The tile's keys are staged in shared memory by a bulk copy started while
+// the previous tile is still being counted.
+constexpr int kGroupBits = 12;
+constexpr int kGroupDigits = 1 << kGroupBits;
+
+template <typename K, int THREADS, int IPT>
+struct TileGroupSmem {
+  static constexpr int TILE = THREADS * IPT;
+  static constexpr int PAD = 16 / sizeof(K);  // the staged range starts on a 16-byte boundary
+  K a[TILE + 2 * PAD];            // staged keys (bulk copy target)
+  K b[TILE];                      // keys partitioned by their low digit
+  // digit counts, then bucket offsets (off[kGroupDigits] = n); after the
+  // scatter: per digit, keys left unsettled by the last two rounds (16-bit halves)
+  uint32_t off[kGroupDigits + 4];
+  uint16_t rep[kGroupDigits];     // position in b of each bucket's current representative
+  uint32_t ws[THREADS / 32 + 1];
+  uint64_t ws64[THREADS / 32 + 1];
+  uint64_t bar;                   // mbarrier of the bulk copies
+  unsigned long long base;
+  // the tile whose copy is in flight (t_next = number of tiles when none is)
+  uint32_t t_next, n_next, lead_next, group_next;
+};
+
+// Thread 0: takes tiles until one fits (bigger ones go to the big list,
+// empty ones are skipped), starts its bulk copy and records it.
+template <typename K, int THREADS, int IPT>
+__device__ void group_fetch(const K *keys, const TilePlan &plan, uint32_t nt, uint32_t *work,
+                            TileGroupSmem<K, THREADS, IPT> &s, uint32_t *big_list, uint32_t *n_big,
+                            unsigned long long *big_keys, uint32_t big_cap, uint32_t *err) {
+  using SM = TileGroupSmem<K, THREADS, IPT>;
+  for (;;) {
+    const uint32_t t = atomicAdd(work, 1u);
+    if (t >= nt) {
+      s.t_next = nt;
+      return;
+    }
+    uint64_t st, en;
+    int nbits;
+    uint32_t group;
+    tile_range(plan, t, nt, &st, &en, &nbits, &group);
+    const uint64_t n = en - st;
+    if (n == 0) continue;
+    if (n > (uint64_t)SM::TILE) {
+      push_big(t, n, big_list, n_big, big_keys, big_cap, err);
+      continue;
+    }
+    // copy the 16-byte aligned cover of keys[st, en) (the key buffers keep
+    // 16 bytes of slack past their last key)
+    const uintptr_t src = reinterpret_cast<uintptr_t>(keys + st);
+    const uintptr_t src0 = src & ~(uintptr_t)15;
+    const uint32_t bytes = (uint32_t)((src + n * sizeof(K) - src0 + 15) & ~(uintptr_t)15);
+    s.t_next = t;
+    s.n_next = (uint32_t)n;
+    s.lead_next = (uint32_t)((src - src0) / sizeof(K));
+    s.group_next = group;
+    fence_proxy_async_smem();
+    bulk_load(s.a, reinterpret_cast<const void *>(src0), bytes, &s.bar);
+    return;
+  }
+}
+
+template <typename K, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS, 2)
+tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<K> out,
+                  uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys,
+                  uint32_t big_cap, uint32_t *err) {
+  using SM = TileGroupSmem<K, THREADS, IPT>;
+  constexpr int DPT = kGroupDigits / THREADS;  // digit counters scanned per thread
+  static_assert(DPT == 4 || DPT == 8 || DPT == 16, "scan uses 16-byte loads");
+  static_assert(SM::TILE <= 4096, "positions and counts are 12/13-bit fields");
+  static_assert(offsetof(SM, off) % 16 == 0 && offsetof(SM, a) == 0, "16-byte aligned arrays");
+  // per-key state: position in b (bits 0-12), group count (bits 13-25),
+  // settled (bit 30), group head (bit 31)
+  constexpr uint32_t POS = 0x1FFFu, SETTLED = 1u << 30, HEAD = 1u << 31;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &s = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t nt = *plan.n_tiles;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&s.bar, 1);
+    group_fetch<K, THREADS, IPT>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (;;) {
+    if (s.t_next >= nt) break;
+    const int n = (int)s.n_next, lead = (int)s.lead_next;
+    const uint32_t group = s.group_next;
+    const bool ok = mbar_wait(&s.bar, parity);
+    // (this barrier also ends the previous tile: all threads are past its output)
+    if (!__syncthreads_and(ok)) {
+      // the copy did not land in time: report, give it one more bounded
+      // wait so that no copy is left in flight, and stop
+      if (tid == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+        mbar_wait(&s.bar, parity);
+      }
+      return;
+    }
+    parity ^= 1u;
+    for (int i = tid; i < kGroupDigits + 4; i += THREADS) s.off[i] = 0;
+    K key[IPT];
+    uint32_t st[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int e = tid + i * THREADS;
+      st[i] = SETTLED;  // keys past n take no part
+      if (e < n) key[i] = s.a[lead + e];
+    }
+    __syncthreads();  // s.a consumed, s.off zeroed
+    if (tid == 0)
+      group_fetch<K, THREADS, IPT>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
+    // digit histogram; the returned old count is the key's rank in its digit
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int e = tid + i * THREADS;
+      if (e < n) st[i] = atomicAdd(&s.off[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of the digit counts (thread t: counters [DPT t, DPT t + DPT))
+    {
+      uint32_t c[DPT];
+#pragma unroll
+      for (int q = 0; q < DPT; q += 4) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(&s.off[DPT * tid + q]);
+        c[q] = v.x; c[q + 1] = v.y; c[q + 2] = v.z; c[q + 3] = v.w;
+      }
+      uint32_t sum = 0;
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) sum += c[q];
+      uint32_t tot;
+      uint32_t run = block_excl_scan<uint32_t, THREADS>(sum, s.ws, &tot);
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        const uint32_t x = c[q];
+        c[q] = run;
+        run += x;
+      }
+#pragma unroll
+      for (int q = 0; q < DPT; q += 4)
+        *reinterpret_cast<uint4 *>(&s.off[DPT * tid + q]) = make_uint4(c[q], c[q + 1], c[q + 2], c[q + 3]);
+      if (tid == 0) s.off[kGroupDigits] = (uint32_t)n;
+    }
+    __syncthreads();
+    // scatter; a bucket's first key becomes its representative and carries
+    // the bucket size
+    uint32_t bsize[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int e = tid + i * THREADS;
+      bsize[i] = 0;
+      if (e < n) {
+        const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
+        const uint32_t lo = s.off[d], p = lo + st[i];
+        s.b[p] = key[i];
+        if (st[i] == 0) {
+          s.rep[d] = (uint16_t)p;
+          bsize[i] = s.off[d + 1] - lo;
+        }
+        st[i] = p;  // unsettled
+      }
+    }
+    __syncthreads();  // s.off (offsets) no longer needed: it now holds the unsettled counts
+#pragma unroll
+    for (int i = 0; i < IPT; ++i)
+      if (bsize[i]) s.off[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = bsize[i];
+    __syncthreads();
+    // rounds: count j of unsettled keys sits in half j & 1 of the digit's word
+    for (uint32_t round = 1;; ++round) {
+      const uint32_t inc = (round & 1) ? 0x10000u : 1u;
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        if (st[i] & SETTLED) continue;
+        const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
+        const uint32_t r = s.rep[d];
+        if (s.b[r] == key[i]) st[i] |= SETTLED | (r == (st[i] & POS) ? HEAD : 0u);
+        else atomicAdd(&s.off[d], inc);
+      }
+      __syncthreads();
+      bool left = false;
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
+        if ((st[i] & HEAD) && ((st[i] >> 13) & 0x1FFFu) == 0) {
+          // this round's representative: its group is the drop of the count
+          const uint32_t w = s.off[d];
+          const uint32_t prev = (round & 1) ? (w & 0xFFFFu) : (w >> 16);
+          const uint32_t cur = (round & 1) ? (w >> 16) : (w & 0xFFFFu);
+          st[i] |= (prev - cur) << 13;
+          s.off[d] = (round & 1) ? (w & 0xFFFF0000u) : (w & 0xFFFFu);
+        }
+        left |= !(st[i] & SETTLED);
+      }
+      if (!__syncthreads_or(left)) break;
+      // next representatives: any unsettled key of the bucket
+#pragma unroll
+      for (int i = 0; i < IPT; ++i)
+        if (!(st[i] & SETTLED)) s.rep[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = (uint16_t)(st[i] & POS);
+      __syncthreads();
+    }
+    // survivors, in key order per thread; one scan gives both the survivor
+    // offsets (low half) and the group total (high half)
+    uint32_t n_groups = 0, n_keep = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (!(st[i] & HEAD)) continue;
+      const uint32_t c = (st[i] >> 13) & 0x1FFFu;
+      ++n_groups;
+      n_keep += c >= out.ci && c <= out.cx;
+    }
+    uint64_t tot2;
+    const uint64_t pre = block_excl_scan<uint64_t, THREADS>(((uint64_t)n_groups << 32) | n_keep,
+                                                            s.ws64, &tot2);
+    uint32_t kb = (uint32_t)pre;
+    const uint32_t ktot = (uint32_t)tot2;
+    if (tid == 0) {
+      s.base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
+      atomicAdd(out.n_distinct, tot2 >> 32);
+    }
+    __syncthreads();
+    const uint64_t base = s.base;
+    if (base + ktot > out.cap) {
+      if (tid == 0) atomicOr(err, ERR_CAPACITY);
+    } else if (n_keep) {
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        if (!(st[i] & HEAD)) continue;
+        const uint32_t c = (st[i] >> 13) & 0x1FFFu;
+        if (c >= out.ci && c <= out.cx) {
+          out.keys[base + kb] = out.mixer.unmix(key[i]);
+          out.counts[base + kb] = c;
+          if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
+          ++kb;
+        }
+      }
+    }
+  }
+}
+
 // Pairs mode: sort every tile of (key, value) pairs in place (keys/vals are
 // read and written at the same positions).  Used to put the survivors in
 // global order and to order signatures by weight.
