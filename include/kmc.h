@@ -131,11 +131,14 @@ int kmc_open(kmc_handle **h, const kmc_params *p);
 
 /* Adds reads held in HOST memory: read i is bases[offsets[i] .. offsets[i+1]),
  * offsets has n_reads+1 non-decreasing entries and offsets[0] == 0.  The
- * bytes are copied (through pinned staging buffers, overlapped with the
- * distribution kernels) before the call returns, so the caller may free them
- * at once.  May be called repeatedly before kmc_count; each call appends.
+ * bytes are copied before the call returns, so the caller may free them at
+ * once.  Pinned (page-locked) input is copied in pieces of up to 256 MiB on
+ * a second stream, the copy of one piece overlapping the distribution of the
+ * one before; pageable input goes through pinned staging buffers.  May be
+ * called repeatedly before kmc_count; each call appends.
  * Errors: KMC_EINVAL (NULL pointer with n_reads > 0), KMC_EINPUT (offsets
- * not non-decreasing or not starting at 0), KMC_ESTATE (after kmc_count
+ * not non-decreasing or not starting at 0; decreasing offsets are found by
+ * the device, after the reads were staged), KMC_ESTATE (after kmc_count
  * without kmc_reset), KMC_ENOMEM, KMC_ECUDA. */
 int kmc_add_reads(kmc_handle *h, const char *bases, const uint64_t *offsets, uint64_t n_reads);
 

@@ -189,7 +189,17 @@ void release_all(Handle &h) {
     h.ds.stage_host[i] = nullptr;
     if (h.ds.stage_free[i]) cudaEventDestroy(h.ds.stage_free[i]);
     h.ds.stage_free[i] = nullptr;
+    if (h.ds.copy_done[i]) cudaEventDestroy(h.ds.copy_done[i]);
+    if (h.ds.buf_free[i]) cudaEventDestroy(h.ds.buf_free[i]);
+    h.ds.copy_done[i] = h.ds.buf_free[i] = nullptr;
   }
+  if (h.ds.go) cudaEventDestroy(h.ds.go);
+  h.ds.go = nullptr;
+  if (h.ds.copy_st) {
+    cudaStreamSynchronize(h.ds.copy_st);
+    cudaStreamDestroy(h.ds.copy_st);
+  }
+  h.ds.copy_st = nullptr;
 }
 
 int validate(const kmc_params *p) {
@@ -260,6 +270,79 @@ int add_device(Handle &h, const char *d_bases, const uint64_t *d_offsets, uint64
 
 }  // namespace
 
+}  // namespace kmc
+
+namespace kmc {
+namespace {
+constexpr uint64_t kHostPieceBytes = 256ull << 20;  // pieces of pinned host input
+
+// Pinned host reads: pieces are copied on a copy stream into two device
+// buffers in turn, the copy of piece i+1 overlapping the distribution of
+// piece i on the handle's stream.
+int add_pinned(Handle &h, const char *bases, const uint64_t *offsets, uint64_t n_reads) {
+  DistScratch &ds = h.ds;
+  const uint64_t piece = std::min<uint64_t>(h.piece_bytes, kHostPieceBytes);
+  std::vector<uint64_t> cut{0};
+  uint64_t max_nb = 0, max_nr = 0;
+  while (cut.back() < n_reads) {
+    const uint64_t r0 = cut.back(), b0 = offsets[r0];
+    const uint64_t *it = std::upper_bound(offsets + r0 + 1, offsets + n_reads + 1, b0 + piece);
+    uint64_t r1 = (uint64_t)(it - offsets) - 1;
+    if (r1 <= r0) r1 = r0 + 1;
+    if (offsets[r1] < b0) return KMC_EINPUT;
+    max_nb = std::max(max_nb, offsets[r1] - b0);
+    max_nr = std::max(max_nr, r1 - r0);
+    cut.push_back(r1);
+  }
+  const size_t n_pieces = cut.size() - 1;
+  const int n_buf = n_pieces > 1 ? 2 : 1;
+  for (int i = 0; i < n_buf; ++i)
+    if (dev_ensure(ds.stage_dev[i], max_nb + 64, h.st) || dev_ensure(ds.offs_dev[i], (max_nr + 1) * 8, h.st))
+      return KMC_ENOMEM;
+  if (!ds.copy_st) {
+    KMC_CUDA_TRY(cudaStreamCreateWithFlags(&ds.copy_st, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      KMC_CUDA_TRY(cudaEventCreateWithFlags(&ds.copy_done[i], cudaEventDisableTiming));
+      KMC_CUDA_TRY(cudaEventCreateWithFlags(&ds.buf_free[i], cudaEventDisableTiming));
+    }
+    KMC_CUDA_TRY(cudaEventCreateWithFlags(&ds.go, cudaEventDisableTiming));
+  }
+  // copies start after everything queued so far (buffer allocations included)
+  KMC_CUDA_TRY(cudaEventRecord(ds.go, h.st));
+  KMC_CUDA_TRY(cudaStreamWaitEvent(ds.copy_st, ds.go, 0));
+  auto copy = [&](size_t i) -> int {
+    const int b = (int)(i & 1);
+    const uint64_t r0 = cut[i], r1 = cut[i + 1], b0 = offsets[r0];
+    if (i >= 2) KMC_CUDA_TRY(cudaStreamWaitEvent(ds.copy_st, ds.buf_free[b], 0));
+    KMC_CUDA_TRY(cudaMemcpyAsync(ds.stage_dev[b].p, bases + b0, offsets[r1] - b0, cudaMemcpyHostToDevice,
+                                 ds.copy_st));
+    KMC_CUDA_TRY(cudaMemcpyAsync(ds.offs_dev[b].p, offsets + r0, (r1 - r0 + 1) * 8, cudaMemcpyHostToDevice,
+                                 ds.copy_st));
+    KMC_CUDA_TRY(cudaEventRecord(ds.copy_done[b], ds.copy_st));
+    return KMC_OK;
+  };
+  int rc = copy(0);
+  if (rc) return rc;
+  for (size_t i = 0; i < n_pieces; ++i) {
+    if (i + 1 < n_pieces && (rc = copy(i + 1))) return rc;
+    const int b = (int)(i & 1);
+    KMC_CUDA_TRY(cudaStreamWaitEvent(h.st, ds.copy_done[b], 0));
+    const uint64_t r0 = cut[i], r1 = cut[i + 1], nr = r1 - r0, b0 = offsets[r0];
+    const char *pbase = static_cast<const char *>(ds.stage_dev[b].p);
+    const uint64_t *poff = as<uint64_t>(ds.offs_dev[b]);
+    if (!h.map_ready) {
+      const uint64_t se = std::min<uint64_t>(nr, kSampleReads);
+      if ((rc = build_bin_map(h, pbase, poff, se, b0, offsets[r0 + se], h.stats.n_reads + r0))) return rc;
+    }
+    if ((rc = distribute_device_piece(h, pbase, poff, nr, b0, offsets[r1], h.stats.n_reads + r0))) return rc;
+    KMC_CUDA_TRY(cudaEventRecord(ds.buf_free[b], h.st));
+  }
+  // later work on the handle's stream may reuse the buffers
+  KMC_CUDA_TRY(cudaEventRecord(ds.copy_done[0], ds.copy_st));
+  KMC_CUDA_TRY(cudaStreamWaitEvent(h.st, ds.copy_done[0], 0));
+  return KMC_OK;
+}
+}  // namespace
 }  // namespace kmc
 
 using namespace kmc;
@@ -400,8 +483,8 @@ int kmc_add_reads(kmc_handle *kh, const char *bases, const uint64_t *offsets, ui
   if (n_reads == 0) return KMC_OK;
   if (!offsets) return KMC_EINVAL;
   if (offsets[0] != 0) return KMC_EINPUT;
-  for (uint64_t i = 0; i < n_reads; ++i)
-    if (offsets[i + 1] < offsets[i]) return KMC_EINPUT;
+  // offsets that decrease are found by the device (ERR_INPUT) while the
+  // reads are marked; the host only checks the piece bounds it copies by
   const uint64_t n_bases = offsets[n_reads];
   if (n_bases && !bases) return KMC_EINVAL;
   DeviceGuard g(h.p.device);
@@ -412,8 +495,12 @@ int kmc_add_reads(kmc_handle *kh, const char *bases, const uint64_t *offsets, ui
   const bool pinned_b = cudaPointerGetAttributes(&at, bases) == cudaSuccess && at.type == cudaMemoryTypeHost;
   cudaGetLastError();
   KMC_CUDA_TRY(cudaEventRecord(h.ev[0], h.st));
+  if (pinned_b) {
+    int rc = add_pinned(h, bases, offsets, n_reads);
+    if (rc) return rc;
+  }
   const uint64_t kPieceBytes = h.piece_bytes;
-  uint64_t r0 = 0;
+  uint64_t r0 = pinned_b ? n_reads : 0;
   while (r0 < n_reads) {
     // reads [r0, r1) with at most kPieceBytes bytes (at least one read)
     const uint64_t b0 = offsets[r0];
@@ -421,6 +508,7 @@ int kmc_add_reads(kmc_handle *kh, const char *bases, const uint64_t *offsets, ui
     uint64_t r1 = (uint64_t)(it - offsets) - 1;
     if (r1 <= r0) r1 = r0 + 1;
     const uint64_t b1 = offsets[r1];
+    if (b1 < b0) return KMC_EINPUT;
     const uint64_t nb = b1 - b0, nr = r1 - r0;
     if (dev_ensure(ds.stage_dev[0], nb + 64, h.st) || dev_ensure(ds.offs_dev[0], (nr + 1) * 8, h.st))
       return KMC_ENOMEM;

@@ -52,6 +52,10 @@ struct DistScratch {
   void *stage_host[2] = {nullptr, nullptr};
   size_t stage_host_cap[2] = {0, 0};
   cudaEvent_t stage_free[2] = {nullptr, nullptr};
+  // pinned host input: pieces are copied on their own stream, one ahead of
+  // the piece being distributed
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_done[2] = {nullptr, nullptr}, buf_free[2] = {nullptr, nullptr}, go = nullptr;
 };
 
 // Per-call scratch of the sorting phase.

@@ -234,6 +234,16 @@ def test_many_pieces_host_and_device(piece_bytes):
     do = torch.from_numpy(w.offsets.astype(np.int64)).cuda()
     with kmc.Counter(28, m=7, n_bins=128, piece_bytes=piece_bytes) as c:
         assert_same(c.add_device(db, do).count().result(), want)
+    # pinned host input: pieces copied on a second stream, one ahead
+    pb = torch.from_numpy(w.bases).pin_memory()
+    po = torch.from_numpy(w.offsets.astype(np.int64)).pin_memory()
+    with kmc.Counter(28, m=7, n_bins=128, piece_bytes=piece_bytes) as c:
+        for _ in range(2):  # twice: the second call reuses the buffers and events
+            kmc.kmc_add_reads_ptr(c.h, pb.data_ptr(), po.data_ptr(), w.n_reads)
+        got2 = c.count().result()
+    want2 = oracle_count(np.concatenate([w.bases, w.bases]),
+                         np.concatenate([w.offsets, w.offsets[1:] + w.offsets[-1]]), 28)
+    assert_same(got2, want2)
 
 
 @pytest.mark.parametrize("k", [21, 28, 40])
