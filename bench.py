@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
+    ap.add_argument("--bins", type=int, default=0,
+                    help="bin count override (profiling a scaled workload at full-size bins)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the batched / served comparisons")
@@ -170,7 +172,7 @@ def run_ours(args, rank, local_rank, world):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = workload(args.scale)
-    k, m, B, ci, cx = w.k, w.m, w.n_bins, w.cutoff_min, w.cutoff_max
+    k, m, B, ci, cx = w.k, w.m, args.bins or w.n_bins, w.cutoff_min, w.cutoff_max
     d_bases = torch.from_numpy(w.bases).to(dev)
     d_offs = torch.from_numpy(w.offsets.view(np.int64)).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -299,7 +301,7 @@ def run_ours(args, rank, local_rank, world):
                    "distinct_kmers": st0["n_distinct"], "super_kmers": st0["n_superkmers"],
                    "x": st0["x_used"], "l2": "inputs (3 GB of reads, 19 GB of keys) exceed L2; no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "scale": args.scale},
+                   "scale": args.scale, "n_bins": B},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "stages": stages,
         "cpu_baseline": cpu, "clocks": clk, "modes": modes,
     }

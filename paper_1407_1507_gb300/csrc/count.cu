@@ -38,10 +38,11 @@ Mixer<K> make_mixer(int key_bits) {
   return m;
 }
 
+// scratch: NULL, or a buffer of n_keys + 2 keys free for the big tiles
 template <typename K, int IPT>
 int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const Mixer<K> &mixer,
                 uint64_t ci, uint64_t cx, DevBuf &out_k, DevBuf &out_c, uint64_t *n_sv_out,
-                K *sorted_out) {
+                K *sorted_out, K *scratch = nullptr) {
   SortScratch &ss = h.ss;
   using SM = TileCountSmem<K, CNT_THREADS, IPT>;
   using BSM = BigSmem<K, NoVal, CNT_THREADS, BIG_IPT>;
@@ -108,7 +109,26 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
   KMC_CUDA_TRY(cudaMemcpyAsync(&bigk, c64 + 2, 8, cudaMemcpyDeviceToHost, h.st));
   KMC_CUDA_TRY(cudaStreamSynchronize(h.st));
   h.stats.n_big_tiles += nbig;
-  if (nbig) {
+  if (nbig && grouped) {
+    // big tiles: split into sub-buckets at their own positions in scratch
+    using BGS = BigGroupSmem<K, GRP_THREADS, GIPT, GIPT>;
+    if (!scratch) {
+      if (dev_ensure(ss.big_scratch, (n_keys + 2) * sizeof(K), h.st)) return KMC_ENOMEM;
+      scratch = as<K>(ss.big_scratch);
+    }
+    static bool battr = false;
+    if (!battr) {
+      KMC_CUDA_TRY(cudaFuncSetAttribute(big_group_kernel<K, GRP_THREADS, GIPT, GIPT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BGS)));
+      battr = true;
+    }
+    StageScope sc(h, KMC_STAGE_BIG_SORT);
+    big_group_kernel<K, GRP_THREADS, GIPT, GIPT><<<std::min<uint32_t>(nbig, (uint32_t)h.sm_count), GRP_THREADS,
+                                                   sizeof(BGS), h.st>>>(
+        keys, plan, as<uint32_t>(ss.big_list), c32 + 1, scratch, out, plan.key_bits, as<uint32_t>(h.err));
+    KMC_COUNT_LAUNCH();
+    KMC_CUDA_TRY(cudaGetLastError());
+  } else if (nbig) {
     if (dev_ensure(ss.big_scratch, (bigk + 1) * sizeof(K), h.st)) return KMC_ENOMEM;
     StageScope sc(h, KMC_STAGE_BIG_SORT);
     big_count_kernel<K, CNT_THREADS, BIG_IPT><<<nbig, CNT_THREADS, sizeof(BSM), h.st>>>(
@@ -178,9 +198,24 @@ struct SortMeta {
   const PieceDesc *pieces = nullptr;
   const uint32_t *group_base = nullptr;
   const uint8_t *group_D = nullptr;
+  // generate + sweep path (x = 0)
+  bool gen = false;
+  size_t n_units = 0;
+  const PartUnit *units = nullptr;
+  const uint64_t *bin_key_base = nullptr;  // first key of each bin in the generated array
+  const uint32_t *sgroup_base = nullptr;   // first super bucket of each bin [bins + 1]
+  uint32_t n_super = 0;
+  // device scratch (zeroed by the caller where noted)
+  unsigned long long *bin_fill = nullptr;      // keys written per bin (zeroed)
+  uint32_t *super_hist = nullptr;              // keys per super bucket (zeroed)
+  unsigned long long *super_base = nullptr;    // scan of super_hist [n_super + 1]
+  unsigned long long *super_cursor = nullptr;  // keys placed per super bucket (zeroed)
 };
 
-int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta *m) {
+// unit_keys > 0 asks for the generate + sweep path (x = 0, units of
+// unit_keys keys); it is taken when the bins' k-mers add up.
+int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta *m,
+               uint32_t unit_keys = 0) {
   SortScratch &ss = h.ss;
   const uint32_t B = h.p.n_bins;
   std::vector<uint32_t> gbase(B + 1);
@@ -188,11 +223,29 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   uint64_t NB = 0;
   for (uint32_t b = 0; b < B; ++b) {
     gD[b] = (uint8_t)digits_for((uint64_t)(h.bin_kmers[b] * keys_per_kmer), key_bits, tile);
+    // the two sweeps place at most SWEEP_BITS_MAX digit bits; bigger bins
+    // get bigger buckets, which the big-tile pass splits further
+    if (unit_keys) gD[b] = (uint8_t)std::min<int>(gD[b], SWEEP_BITS_MAX);
     gbase[b] = (uint32_t)NB;
     NB += 1ull << gD[b];
   }
   gbase[B] = (uint32_t)NB;
   if (NB >= 0xFFFFFFF0ull) return KMC_EINVAL;
+  std::vector<uint64_t> kbase(B + 1, 0);
+  std::vector<uint32_t> sbase(B + 1, 0);
+  std::vector<PartUnit> units;
+  bool gen = unit_keys > 0;
+  if (gen) {
+    for (uint32_t b = 0; b < B; ++b) {
+      kbase[b + 1] = kbase[b] + h.bin_kmers[b];
+      sbase[b + 1] = sbase[b] + (1u << std::min<int>(gD[b], SWEEP_UPPER));
+      for (uint64_t o = 0; o < h.bin_kmers[b]; o += unit_keys)
+        units.push_back({kbase[b] + o, (uint32_t)std::min<uint64_t>(unit_keys, h.bin_kmers[b] - o), b});
+    }
+    if (kbase[B] != h.stats.n_kmer_positions) gen = false;
+    if (!gen) units.clear();
+  }
+  const uint32_t n_super = gen ? sbase[B] : 0;
   std::vector<Chunk> chunks;
   std::vector<PieceDesc> pds;
   for (size_t p = 0; p < h.pieces.size(); ++p) {
@@ -204,20 +257,30 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
         chunks.push_back({r, (uint32_t)std::min<uint64_t>(KX_RECORDS_PER_CHUNK, rb[b + 1] - r),
                           (uint32_t)p, b, 0});
   }
-  const size_t meta_bytes = (chunks.size() + 1) * sizeof(Chunk) + (pds.size() + 1) * sizeof(PieceDesc) +
-                            (B + 1) * 4 + B + 64;
+  auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t o_pd = up16((chunks.size() + 1) * sizeof(Chunk));
+  const size_t o_gb = o_pd + up16((pds.size() + 1) * sizeof(PieceDesc));
+  const size_t o_gd = o_gb + up16((B + 1) * 4);
+  const size_t o_un = o_gd + up16(B + 1);
+  const size_t o_kb = o_un + up16((units.size() + 1) * sizeof(PartUnit));
+  const size_t o_sg = o_kb + up16((B + 1) * 8);
+  const size_t o_bf = o_sg + up16((B + 1) * 4);  // device-only from here on
+  const size_t o_sh = o_bf + up16((B + 1) * 8);
+  const size_t o_sc = o_sh + up16((n_super + 1) * 4);
+  const size_t o_sb = o_sc + up16((n_super + 1) * 8);
+  const size_t meta_bytes = o_sb + up16((n_super + 2) * 8);
   if (dev_ensure(ss.counters, 64, h.st) || dev_ensure(ss.cursor, meta_bytes, h.st) ||
       dev_ensure(ss.hist, NB * 4 + 4, h.st))
     return KMC_ENOMEM;
-  std::vector<uint8_t> meta(meta_bytes);
-  const size_t o_pd = (chunks.size() + 1) * sizeof(Chunk);
-  const size_t o_gb = o_pd + (pds.size() + 1) * sizeof(PieceDesc);
-  const size_t o_gd = o_gb + (B + 1) * 4;
+  std::vector<uint8_t> meta(o_bf);  // the fill counters are zeroed on the device
   memcpy(meta.data(), chunks.data(), chunks.size() * sizeof(Chunk));
   memcpy(meta.data() + o_pd, pds.data(), pds.size() * sizeof(PieceDesc));
   memcpy(meta.data() + o_gb, gbase.data(), (B + 1) * 4);
   memcpy(meta.data() + o_gd, gD.data(), B);
-  KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta.data(), meta_bytes, cudaMemcpyHostToDevice, h.st));
+  if (!units.empty()) memcpy(meta.data() + o_un, units.data(), units.size() * sizeof(PartUnit));
+  memcpy(meta.data() + o_kb, kbase.data(), (B + 1) * 8);
+  memcpy(meta.data() + o_sg, sbase.data(), (B + 1) * 4);
+  KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta.data(), o_bf, cudaMemcpyHostToDevice, h.st));
   char *base = static_cast<char *>(ss.cursor.p);
   m->n_chunks = chunks.size();
   m->NB = NB;
@@ -225,6 +288,18 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   m->pieces = reinterpret_cast<const PieceDesc *>(base + o_pd);
   m->group_base = reinterpret_cast<const uint32_t *>(base + o_gb);
   m->group_D = reinterpret_cast<const uint8_t *>(base + o_gd);
+  m->gen = gen;
+  m->n_units = units.size();
+  m->units = reinterpret_cast<const PartUnit *>(base + o_un);
+  m->bin_key_base = reinterpret_cast<const uint64_t *>(base + o_kb);
+  m->sgroup_base = reinterpret_cast<const uint32_t *>(base + o_sg);
+  m->n_super = n_super;
+  m->bin_fill = reinterpret_cast<unsigned long long *>(base + o_bf);
+  m->super_hist = reinterpret_cast<uint32_t *>(base + o_sh);
+  m->super_cursor = reinterpret_cast<unsigned long long *>(base + o_sc);
+  m->super_base = reinterpret_cast<unsigned long long *>(base + o_sb);
+  if (gen)  // fill counters, super histogram and cursors start at zero
+    KMC_CUDA_TRY(cudaMemsetAsync(base + o_bf, 0, o_sb - o_bf, h.st));
   ss.dbg_group_base = gbase;
   return KMC_OK;
 }
@@ -269,7 +344,7 @@ int sort_phase_x0(Handle &h) {
   const uint64_t n_keys = h.stats.n_kmer_positions;
   h.stats.n_sorted_keys = n_keys;
   SortMeta meta;
-  int rc = build_meta(h, key_bits, TILE, 1.0, &meta);
+  int rc = build_meta(h, key_bits, TILE, 1.0, &meta, SweepTraits<K>::TILE);
   if (rc) return rc;
   KxArgs<K> a;
   a.n_chunks_dyn = nullptr;
@@ -283,8 +358,63 @@ int sort_phase_x0(Handle &h) {
   save_debug_mixer(h, a.mixer);
   const uint64_t NB = meta.NB;
   uint32_t *hist = as<uint32_t>(ss.hist);
-  KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));
-  if (meta.n_chunks) {
+  if (dev_ensure(ss.keys, (n_keys + 2) * sizeof(K), h.st)) return KMC_ENOMEM;  // 16 B slack
+  K *keys = as<K>(ss.keys);    // the keys the tiles are counted from
+  K *scratch = nullptr;        // free space for the big tiles
+  if (meta.n_chunks && meta.gen) {
+    // keys built once, into their bins' ranges; upper digits counted
+    if (dev_ensure(ss.keys_gen, (n_keys + 2) * sizeof(K), h.st)) return KMC_ENOMEM;
+    K *gen_keys = as<K>(ss.keys_gen);
+    {
+      StageScope sc(h, KMC_STAGE_KX_COUNT);
+      kx0_gen_kernel<K><<<(unsigned)meta.n_chunks, KX_THREADS, 0, h.st>>>(
+          a, meta.sgroup_base, meta.super_hist, meta.bin_key_base, meta.bin_fill, gen_keys, n_keys,
+          as<uint32_t>(h.err));
+      KMC_COUNT_LAUNCH();
+      KMC_CUDA_TRY(cudaGetLastError());
+    }
+    if (dev_ensure(ss.scan_tmp, scan_tmp_words(meta.n_super) * 8, h.st)) return KMC_ENOMEM;
+    KMC_CUDA_TRY(device_excl_scan_u32(meta.super_hist, reinterpret_cast<uint64_t *>(meta.super_base),
+                                      meta.n_super, as<uint64_t>(ss.scan_tmp), h.st));
+    SweepArgs<K> sa;
+    sa.key_bits = key_bits;
+    sa.n_keys = n_keys;
+    sa.group_D = meta.group_D;
+    sa.group_base = meta.group_base;
+    sa.sgroup_base = meta.sgroup_base;
+    sa.n_bins = h.p.n_bins;
+    sa.super_base = meta.super_base;
+    sa.super_cursor = meta.super_cursor;
+    sa.fine_hist = hist;
+    sa.units = meta.units;
+    sa.n_units = (uint32_t)meta.n_units;
+    sa.n_super = meta.n_super;
+    sa.err = as<uint32_t>(h.err);
+    static bool attr = false;
+    if (!attr) {
+      KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_sweep_kernel<K, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(SweepSmem<K>)));
+      KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_sweep_kernel<K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(SweepSmem<K>)));
+      attr = true;
+    }
+    StageScope sc(h, KMC_STAGE_KX_SCATTER);
+    // upper digits: generated keys -> super buckets (in ss.keys)
+    sa.in = gen_keys;
+    sa.out = keys;
+    kx0_sweep_kernel<K, 0><<<(unsigned)std::min<uint64_t>(h.sm_count, meta.n_units), SWEEP_THREADS,
+                             sizeof(SweepSmem<K>), h.st>>>(sa);
+    KMC_COUNT_LAUNCH();
+    // lower digits: super buckets -> final buckets (back in keys_gen)
+    sa.in = keys;
+    sa.out = gen_keys;
+    kx0_sweep_kernel<K, 1><<<meta.n_super, SWEEP_THREADS, sizeof(SweepSmem<K>), h.st>>>(sa);
+    KMC_COUNT_LAUNCH();
+    KMC_CUDA_TRY(cudaGetLastError());
+    scratch = keys;
+    keys = gen_keys;
+  } else if (meta.n_chunks) {
+    KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));
     StageScope sc(h, KMC_STAGE_KX_COUNT);
     kx0_count_kernel<K><<<(unsigned)meta.n_chunks, KX_THREADS, 0, h.st>>>(a, hist);
     KMC_COUNT_LAUNCH();
@@ -297,10 +427,8 @@ int sort_phase_x0(Handle &h) {
                     ss.flag_scan, ss.tile_first, ss.scan_tmp, &n_tiles_dev);
   }
   if (rc) return rc;
-  KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));  // hist becomes the per-bucket cursor
-  if (dev_ensure(ss.keys, (n_keys + 2) * sizeof(K), h.st)) return KMC_ENOMEM;  // 16 B slack
-  K *keys = as<K>(ss.keys);
-  if (meta.n_chunks) {
+  if (meta.n_chunks && !meta.gen) {
+    KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));  // hist becomes the per-bucket cursor
     static bool attr = false;
     if (!attr) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -330,7 +458,7 @@ int sort_phase_x0(Handle &h) {
   uint64_t n_sv = 0;
   h.stats.n_big_tiles = 0;
   rc = count_tiles<K, IPT>(h, plan, n_keys, keys, a.mixer, h.p.cutoff_min, h.p.cutoff_max,
-                           ss.sv_keys, ss.sv_counts, &n_sv, sorted_out);
+                           ss.sv_keys, ss.sv_counts, &n_sv, sorted_out, scratch);
   if (rc) return rc;
   uint32_t nt = 0;
   KMC_CUDA_TRY(cudaMemcpyAsync(&nt, n_tiles_dev, 4, cudaMemcpyDeviceToHost, h.st));

@@ -246,6 +246,269 @@ kx0_scatter_kernel(KxArgs<K> a, const uint64_t *__restrict__ bucket_base,
   }
 }
 
+// ------------------------------------------------- x = 0, generate + partition
+// The same result as kx0_count + kx0_scatter with each key built once and
+// moved by two coalesced radix partition sweeps.  A bin's D digit bits
+// (D <= SWEEP_BITS_MAX) split into an upper digit of S = min(D, 8) bits
+// ("super buckets") and a lower one of E = D - S bits.
+//  * kx0_gen_kernel writes every chunk's mixed canonical k-mers contiguously
+//    into its bin's range of an unpartitioned array (one atomic per chunk
+//    reserves the range; writes are coalesced) and counts upper digits.
+//  * kx0_sweep_kernel<0> moves a bin's keys into its super buckets, in
+//    tiles of SWEEP_TILE keys: the tile is sorted by digit in shared memory
+//    (one atomic per key gives the rank), one global atomic per digit
+//    reserves the tile's share of each super bucket, and the keys go out in
+//    digit order, so consecutive threads write consecutive addresses.
+//  * kx0_sweep_kernel<1> does the same inside each super bucket (one CTA
+//    owns it: a histogram pass, then the sweep with cursors in shared
+//    memory) for the lower digit, which puts every key in its final bucket,
+//    and stores the final bucket sizes.
+
+constexpr int SWEEP_THREADS = 1024;
+constexpr int SWEEP_UPPER = 8;                  // bits of the upper digit
+constexpr int SWEEP_BITS_MAX = 2 * SWEEP_UPPER; // digit bits per bin this path supports
+
+template <typename K>
+struct SweepTraits {
+  static constexpr int IPT = 128 / (int)sizeof(K);        // 16 u64 / 8 u128 keys per thread
+  static constexpr int TILE = SWEEP_THREADS * IPT;        // keys per tile (128 KB)
+};
+
+struct PartUnit {
+  uint64_t start;  // first key (index into the unpartitioned array)
+  uint32_t n;      // keys
+  uint32_t bin;
+};
+
+struct KxGenSmem {
+  uint32_t h[1 << SWEEP_UPPER];
+  uint32_t bt[KX_RECORDS_PER_CHUNK / 32 + 1];  // k-mers per 32-record batch, then offsets
+  unsigned long long base;
+};
+
+// Upper digit of a key of a bin with D digit bits (S = min(D, 8) top bits).
+template <typename K>
+__device__ __forceinline__ uint32_t upper_digit(K key, int key_bits, int D) {
+  const int S = D < SWEEP_UPPER ? D : SWEEP_UPPER;
+  return S ? (uint32_t)(uint64_t)(key >> (key_bits - S)) : 0u;
+}
+// Lower digit (the E = D - S bits below the upper digit).
+template <typename K>
+__device__ __forceinline__ uint32_t lower_digit(K key, int key_bits, int D) {
+  const int S = D < SWEEP_UPPER ? D : SWEEP_UPPER;
+  const int E = D - S;
+  return E ? (uint32_t)(uint64_t)(key >> (key_bits - D)) & ((1u << E) - 1u) : 0u;
+}
+
+// sgroup_base[bin]: index of the bin's first super bucket (2^S per bin).
+template <typename K>
+__global__ void __launch_bounds__(KX_THREADS)
+kx0_gen_kernel(KxArgs<K> a, const uint32_t *__restrict__ sgroup_base, uint32_t *__restrict__ super_hist,
+               const uint64_t *__restrict__ bin_key_base, unsigned long long *__restrict__ bin_fill,
+               K *__restrict__ keys, uint64_t n_keys, uint32_t *err) {
+  __shared__ KxGenSmem s;
+  if (a.n_chunks_dyn && blockIdx.x >= *a.n_chunks_dyn) return;
+  const Chunk c = a.chunks[blockIdx.x];
+  const int D = a.group_D[c.bin];
+  const uint32_t NS = 1u << (D < SWEEP_UPPER ? D : SWEEP_UPPER);
+  const PieceDesc pd = a.pieces[c.piece];
+  const unsigned w = threadIdx.x >> 5, lane = lane_id();
+  const uint64_t r_end = c.r0 + c.n_rec;
+  for (uint32_t i = threadIdx.x; i < NS; i += KX_THREADS) s.h[i] = 0;
+  // k-mers per batch of 32 records, then the chunk's range in its bin
+  for (uint64_t r = c.r0 + 32ull * w; r < r_end; r += 32ull * (KX_THREADS / 32)) {
+    const RecBatch b = load_batch(pd.index, r, r_end);
+    if (lane == 0) s.bt[(r - c.r0) / 32] = b.total;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t nb = (c.n_rec + 31) / 32;
+    uint32_t run = 0;
+    for (uint32_t i = 0; i < nb; ++i) {
+      const uint32_t t = s.bt[i];
+      s.bt[i] = run;
+      run += t;
+    }
+    s.base = bin_key_base[c.bin] + atomicAdd(&bin_fill[c.bin], (unsigned long long)run);
+  }
+  __syncthreads();
+  const uint64_t base = s.base;
+  for (uint64_t r = c.r0 + 32ull * w; r < r_end; r += 32ull * (KX_THREADS / 32)) {
+    const RecBatch b = load_batch(pd.index, r, r_end);
+    const uint64_t kb = base + s.bt[(r - c.r0) / 32];
+    for (uint32_t it = 0; 32 * it < b.total; ++it) {
+      uint32_t rec, j;
+      locate(b, it, &rec, &j);
+      const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
+      if (32 * it + lane >= b.total) continue;
+      const K key = a.mixer.mix(canonical_kmer<K>(pd.words + woff, j, a.k));
+      const uint64_t p = kb + 32 * it + lane;
+      if (p < n_keys) keys[p] = key; else atomicOr(err, ERR_CAPACITY);
+      atomicAdd(&s.h[upper_digit<K>(key, a.key_bits, D)], 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t *hb = super_hist + sgroup_base[c.bin];
+  for (uint32_t i = threadIdx.x; i < NS; i += KX_THREADS)
+    if (s.h[i]) atomicAdd(&hb[i], s.h[i]);
+}
+
+template <typename K>
+struct SweepSmem {
+  K sorted[SweepTraits<K>::TILE];         // the tile in digit order
+  uint32_t h[1 << SWEEP_UPPER];           // tile digit counts
+  uint32_t lstart[(1 << SWEEP_UPPER) + 1];  // tile digit starts
+  unsigned long long gpos[1 << SWEEP_UPPER];  // global position of each digit's run
+  unsigned long long cur[1 << SWEEP_UPPER];   // MODE 1: the super bucket's cursors
+  uint32_t ws[SWEEP_THREADS / 32 + 1];
+  uint32_t bin;
+};
+
+// Arguments of both sweeps.
+template <typename K>
+struct SweepArgs {
+  const K *in;
+  K *out;
+  uint64_t n_keys;
+  int key_bits;
+  const uint8_t *group_D;        // digit bits per bin
+  const uint32_t *group_base;    // first final bucket of each bin
+  const uint32_t *sgroup_base;   // first super bucket of each bin [bins + 1]
+  uint32_t n_bins;
+  const unsigned long long *super_base;  // first key of each super bucket [n_super + 1]
+  unsigned long long *super_cursor;      // MODE 0: keys placed per super bucket
+  uint32_t *fine_hist;                   // MODE 1: final bucket sizes (written)
+  const PartUnit *units;                 // MODE 0: the bins' tiles
+  uint32_t n_units;
+  uint32_t n_super;
+  uint32_t *err;
+};
+
+// One tile of n keys at in[st ..]: digits (MODE 0 upper, MODE 1 lower),
+// the tile sorted by digit in shared memory, each digit's run written at
+// gpos[digit] (filled by reserve(), called by thread 0..255 once the tile
+// histogram is in s.h; reserve(t) returns the run's global start).
+template <typename K, int MODE, typename R>
+__device__ __forceinline__ void sweep_tile(const SweepArgs<K> &a, SweepSmem<K> &s, uint64_t st, uint32_t n,
+                                           int D, R reserve) {
+  constexpr int IPT = SweepTraits<K>::IPT;
+  const int tid = threadIdx.x;
+  const int nd = 1 << (MODE == 0 ? (D < SWEEP_UPPER ? D : SWEEP_UPPER) : (D - (D < SWEEP_UPPER ? D : SWEEP_UPPER)));
+  for (int i = tid; i < nd; i += SWEEP_THREADS) s.h[i] = 0;
+  K key[IPT];
+  uint16_t rank[IPT];
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t e = tid + i * SWEEP_THREADS;
+    if (e < n) key[i] = a.in[st + e];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t e = tid + i * SWEEP_THREADS;
+    if (e < n) {
+      const uint32_t d = MODE == 0 ? upper_digit<K>(key[i], a.key_bits, D) : lower_digit<K>(key[i], a.key_bits, D);
+      rank[i] = (uint16_t)atomicAdd(&s.h[d], 1u);
+    }
+  }
+  __syncthreads();
+  // digit starts inside the tile (warp scans over the <= 256 counters) and
+  // the runs' global places
+  if (tid < (1 << SWEEP_UPPER)) {
+    const uint32_t c = tid < nd ? s.h[tid] : 0u;
+    uint32_t inc = warp_incl_scan(c);
+    if ((tid & 31) == 31) s.ws[tid >> 5] = inc;
+    __syncwarp();
+    s.lstart[tid] = inc - c;  // warp-local for now
+    if (tid < nd) s.gpos[tid] = c ? reserve(tid, c) : 0ull;
+  }
+  __syncthreads();
+  if (tid < (1 << SWEEP_UPPER)) {
+    uint32_t add = 0;
+    for (int w = 0; w < (tid >> 5); ++w) add += s.ws[w];
+    s.lstart[tid] += add;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t e = tid + i * SWEEP_THREADS;
+    if (e < n) {
+      const uint32_t d = MODE == 0 ? upper_digit<K>(key[i], a.key_bits, D) : lower_digit<K>(key[i], a.key_bits, D);
+      s.sorted[s.lstart[d] + rank[i]] = key[i];
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += SWEEP_THREADS) {
+    const K k = s.sorted[i];
+    const uint32_t d = MODE == 0 ? upper_digit<K>(k, a.key_bits, D) : lower_digit<K>(k, a.key_bits, D);
+    const uint64_t p = s.gpos[d] + (i - s.lstart[d]);
+    if (p < a.n_keys) a.out[p] = k; else atomicOr(a.err, ERR_CAPACITY);
+  }
+  __syncthreads();
+}
+
+// MODE 0: persistent CTAs over the bins' tiles (units).  MODE 1: one CTA per
+// super bucket.
+template <typename K, int MODE>
+__global__ void __launch_bounds__(SWEEP_THREADS, 1) kx0_sweep_kernel(SweepArgs<K> a) {
+  constexpr int TILE = SweepTraits<K>::TILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SweepSmem<K> &s = *reinterpret_cast<SweepSmem<K> *>(smem_raw);
+  const int tid = threadIdx.x;
+  if (MODE == 0) {
+    for (uint32_t u = blockIdx.x; u < a.n_units; u += gridDim.x) {
+      const PartUnit un = a.units[u];
+      const int D = (int)a.group_D[un.bin];
+      const uint32_t sb0 = a.sgroup_base[un.bin];
+      sweep_tile<K, 0>(a, s, un.start, un.n, D, [&](uint32_t d, uint32_t c) -> unsigned long long {
+        return a.super_base[sb0 + d] + atomicAdd(&a.super_cursor[sb0 + d], (unsigned long long)c);
+      });
+    }
+  } else {
+    const uint32_t sb = blockIdx.x;
+    if (sb >= a.n_super) return;
+    if (tid == 0) {
+      uint32_t lo = 0, hi = a.n_bins;  // bin holding super bucket sb
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (a.sgroup_base[mid] <= sb) lo = mid; else hi = mid;
+      }
+      s.bin = lo;
+    }
+    __syncthreads();
+    const uint32_t bin = s.bin;
+    const int D = (int)a.group_D[bin];
+    const int S = D < SWEEP_UPPER ? D : SWEEP_UPPER;
+    const int E = D - S;
+    const uint64_t st = a.super_base[sb], en = a.super_base[sb + 1];
+    // histogram of the lower digits over the whole super bucket
+    for (int i = tid; i < (1 << E); i += SWEEP_THREADS) s.h[i] = 0;
+    __syncthreads();
+    for (uint64_t e = st + tid; e < en; e += SWEEP_THREADS)
+      atomicAdd(&s.h[lower_digit<K>(a.in[e], a.key_bits, D)], 1u);
+    __syncthreads();
+    // final bucket sizes, and the cursors (exclusive prefix from st)
+    const uint32_t fb = a.group_base[bin] + ((sb - a.sgroup_base[bin]) << E);
+    if (tid == 0) {
+      unsigned long long run = st;
+      for (int i = 0; i < (1 << E); ++i) {
+        a.fine_hist[fb + i] = s.h[i];
+        s.cur[i] = run;
+        run += s.h[i];
+      }
+    }
+    __syncthreads();
+    for (uint64_t t0 = st; t0 < en; t0 += TILE) {
+      const uint32_t n = (uint32_t)((en - t0) < (uint64_t)TILE ? (en - t0) : (uint64_t)TILE);
+      sweep_tile<K, 1>(a, s, t0, n, D, [&](uint32_t d, uint32_t c) -> unsigned long long {
+        const unsigned long long g = s.cur[d];
+        s.cur[d] = g + c;  // only thread d touches cursor d
+        return g;
+      });
+    }
+  }
+}
+
 // ------------------------------------------------------------ (k,x)-mers
 // Sect. 2.3: a super k-mer is split into as few (k,x)-mers as possible:
 // runs of k-mers of one orientation (direct when the k-mer is not larger

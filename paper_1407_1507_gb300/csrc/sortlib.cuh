@@ -564,19 +564,163 @@ __device__ void group_fetch(const K *keys, const TilePlan &plan, uint32_t nt, ui
   }
 }
 
+// Counts the n keys at s.a[lead ..] of one tile (all threads; the caller
+// has passed a barrier after the previous tile's output).  Thread 0 calls
+// after_load() once the keys are in registers and s.a may be refilled.
+template <typename K, int THREADS, int IPT, typename F>
+__device__ __forceinline__ void group_core(TileGroupSmem<K, THREADS, IPT> &s, int n, int lead, uint32_t group,
+                                           const CountOut<K> &out, uint32_t *err, F after_load) {
+  constexpr int DPT = kGroupDigits / THREADS;  // digit counters scanned per thread
+  static_assert(DPT == 4 || DPT == 8 || DPT == 16, "scan uses 16-byte loads");
+  static_assert(TileGroupSmem<K, THREADS, IPT>::TILE <= 4096, "positions and counts are 12/13-bit fields");
+  // per-key state: position in b (bits 0-12), group count (bits 13-25),
+  // settled (bit 30), group head (bit 31)
+  constexpr uint32_t POS = 0x1FFFu, SETTLED = 1u << 30, HEAD = 1u << 31;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kGroupDigits + 4; i += THREADS) s.off[i] = 0;
+  K key[IPT];
+  uint32_t st[IPT];
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const int e = tid + i * THREADS;
+    st[i] = SETTLED;  // keys past n take no part
+    if (e < n) key[i] = s.a[lead + e];
+  }
+  __syncthreads();  // s.a consumed, s.off zeroed
+  if (tid == 0) after_load();
+  // digit histogram; the returned old count is the key's rank in its digit
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const int e = tid + i * THREADS;
+    if (e < n) st[i] = atomicAdd(&s.off[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)], 1u);
+  }
+  __syncthreads();
+  // exclusive scan of the digit counts (thread t: counters [DPT t, DPT t + DPT))
+  {
+    uint32_t c[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; q += 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(&s.off[DPT * tid + q]);
+      c[q] = v.x; c[q + 1] = v.y; c[q + 2] = v.z; c[q + 3] = v.w;
+    }
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) sum += c[q];
+    uint32_t tot;
+    uint32_t run = block_excl_scan<uint32_t, THREADS>(sum, s.ws, &tot);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const uint32_t x = c[q];
+      c[q] = run;
+      run += x;
+    }
+#pragma unroll
+    for (int q = 0; q < DPT; q += 4)
+      *reinterpret_cast<uint4 *>(&s.off[DPT * tid + q]) = make_uint4(c[q], c[q + 1], c[q + 2], c[q + 3]);
+    if (tid == 0) s.off[kGroupDigits] = (uint32_t)n;
+  }
+  __syncthreads();
+  // scatter; a bucket's first key becomes its representative and carries
+  // the bucket size
+  uint32_t bsize[IPT];
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const int e = tid + i * THREADS;
+    bsize[i] = 0;
+    if (e < n) {
+      const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
+      const uint32_t lo = s.off[d], p = lo + st[i];
+      s.b[p] = key[i];
+      if (st[i] == 0) {
+        s.rep[d] = (uint16_t)p;
+        bsize[i] = s.off[d + 1] - lo;
+      }
+      st[i] = p;  // unsettled
+    }
+  }
+  __syncthreads();  // s.off (offsets) no longer needed: it now holds the unsettled counts
+#pragma unroll
+  for (int i = 0; i < IPT; ++i)
+    if (bsize[i]) s.off[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = bsize[i];
+  __syncthreads();
+  // rounds: count j of unsettled keys sits in half j & 1 of the digit's word
+  for (uint32_t round = 1;; ++round) {
+    const uint32_t inc = (round & 1) ? 0x10000u : 1u;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (st[i] & SETTLED) continue;
+      const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
+      const uint32_t r = s.rep[d];
+      if (s.b[r] == key[i]) st[i] |= SETTLED | (r == (st[i] & POS) ? HEAD : 0u);
+      else atomicAdd(&s.off[d], inc);
+    }
+    __syncthreads();
+    bool left = false;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
+      if ((st[i] & HEAD) && ((st[i] >> 13) & 0x1FFFu) == 0) {
+        // this round's representative: its group is the drop of the count
+        const uint32_t w = s.off[d];
+        const uint32_t prev = (round & 1) ? (w & 0xFFFFu) : (w >> 16);
+        const uint32_t cur = (round & 1) ? (w >> 16) : (w & 0xFFFFu);
+        st[i] |= (prev - cur) << 13;
+        s.off[d] = (round & 1) ? (w & 0xFFFF0000u) : (w & 0xFFFFu);
+      }
+      left |= !(st[i] & SETTLED);
+    }
+    if (!__syncthreads_or(left)) break;
+    // next representatives: any unsettled key of the bucket
+#pragma unroll
+    for (int i = 0; i < IPT; ++i)
+      if (!(st[i] & SETTLED)) s.rep[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = (uint16_t)(st[i] & POS);
+    __syncthreads();
+  }
+  // survivors, in key order per thread; one scan gives both the survivor
+  // offsets (low half) and the group total (high half)
+  uint32_t n_groups = 0, n_keep = 0;
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    if (!(st[i] & HEAD)) continue;
+    const uint32_t c = (st[i] >> 13) & 0x1FFFu;
+    ++n_groups;
+    n_keep += c >= out.ci && c <= out.cx;
+  }
+  uint64_t tot2;
+  const uint64_t pre = block_excl_scan<uint64_t, THREADS>(((uint64_t)n_groups << 32) | n_keep,
+                                                          s.ws64, &tot2);
+  uint32_t kb = (uint32_t)pre;
+  const uint32_t ktot = (uint32_t)tot2;
+  if (tid == 0) {
+    s.base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
+    atomicAdd(out.n_distinct, tot2 >> 32);
+  }
+  __syncthreads();
+  const uint64_t base = s.base;
+  if (base + ktot > out.cap) {
+    if (tid == 0) atomicOr(err, ERR_CAPACITY);
+  } else if (n_keep) {
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (!(st[i] & HEAD)) continue;
+      const uint32_t c = (st[i] >> 13) & 0x1FFFu;
+      if (c >= out.ci && c <= out.cx) {
+        out.keys[base + kb] = out.mixer.unmix(key[i]);
+        out.counts[base + kb] = c;
+        if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
+        ++kb;
+      }
+    }
+  }
+}
+
 template <typename K, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS, 2)
 tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<K> out,
                   uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys,
                   uint32_t big_cap, uint32_t *err) {
   using SM = TileGroupSmem<K, THREADS, IPT>;
-  constexpr int DPT = kGroupDigits / THREADS;  // digit counters scanned per thread
-  static_assert(DPT == 4 || DPT == 8 || DPT == 16, "scan uses 16-byte loads");
-  static_assert(SM::TILE <= 4096, "positions and counts are 12/13-bit fields");
   static_assert(offsetof(SM, off) % 16 == 0 && offsetof(SM, a) == 0, "16-byte aligned arrays");
-  // per-key state: position in b (bits 0-12), group count (bits 13-25),
-  // settled (bit 30), group head (bit 31)
-  constexpr uint32_t POS = 0x1FFFu, SETTLED = 1u << 30, HEAD = 1u << 31;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const uint32_t nt = *plan.n_tiles;
@@ -603,142 +747,9 @@ tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
       return;
     }
     parity ^= 1u;
-    for (int i = tid; i < kGroupDigits + 4; i += THREADS) s.off[i] = 0;
-    K key[IPT];
-    uint32_t st[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      const int e = tid + i * THREADS;
-      st[i] = SETTLED;  // keys past n take no part
-      if (e < n) key[i] = s.a[lead + e];
-    }
-    __syncthreads();  // s.a consumed, s.off zeroed
-    if (tid == 0)
+    group_core<K, THREADS, IPT>(s, n, lead, group, out, err, [&]() {
       group_fetch<K, THREADS, IPT>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
-    // digit histogram; the returned old count is the key's rank in its digit
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      const int e = tid + i * THREADS;
-      if (e < n) st[i] = atomicAdd(&s.off[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)], 1u);
-    }
-    __syncthreads();
-    // exclusive scan of the digit counts (thread t: counters [DPT t, DPT t + DPT))
-    {
-      uint32_t c[DPT];
-#pragma unroll
-      for (int q = 0; q < DPT; q += 4) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(&s.off[DPT * tid + q]);
-        c[q] = v.x; c[q + 1] = v.y; c[q + 2] = v.z; c[q + 3] = v.w;
-      }
-      uint32_t sum = 0;
-#pragma unroll
-      for (int q = 0; q < DPT; ++q) sum += c[q];
-      uint32_t tot;
-      uint32_t run = block_excl_scan<uint32_t, THREADS>(sum, s.ws, &tot);
-#pragma unroll
-      for (int q = 0; q < DPT; ++q) {
-        const uint32_t x = c[q];
-        c[q] = run;
-        run += x;
-      }
-#pragma unroll
-      for (int q = 0; q < DPT; q += 4)
-        *reinterpret_cast<uint4 *>(&s.off[DPT * tid + q]) = make_uint4(c[q], c[q + 1], c[q + 2], c[q + 3]);
-      if (tid == 0) s.off[kGroupDigits] = (uint32_t)n;
-    }
-    __syncthreads();
-    // scatter; a bucket's first key becomes its representative and carries
-    // the bucket size
-    uint32_t bsize[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      const int e = tid + i * THREADS;
-      bsize[i] = 0;
-      if (e < n) {
-        const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
-        const uint32_t lo = s.off[d], p = lo + st[i];
-        s.b[p] = key[i];
-        if (st[i] == 0) {
-          s.rep[d] = (uint16_t)p;
-          bsize[i] = s.off[d + 1] - lo;
-        }
-        st[i] = p;  // unsettled
-      }
-    }
-    __syncthreads();  // s.off (offsets) no longer needed: it now holds the unsettled counts
-#pragma unroll
-    for (int i = 0; i < IPT; ++i)
-      if (bsize[i]) s.off[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = bsize[i];
-    __syncthreads();
-    // rounds: count j of unsettled keys sits in half j & 1 of the digit's word
-    for (uint32_t round = 1;; ++round) {
-      const uint32_t inc = (round & 1) ? 0x10000u : 1u;
-#pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        if (st[i] & SETTLED) continue;
-        const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
-        const uint32_t r = s.rep[d];
-        if (s.b[r] == key[i]) st[i] |= SETTLED | (r == (st[i] & POS) ? HEAD : 0u);
-        else atomicAdd(&s.off[d], inc);
-      }
-      __syncthreads();
-      bool left = false;
-#pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
-        if ((st[i] & HEAD) && ((st[i] >> 13) & 0x1FFFu) == 0) {
-          // this round's representative: its group is the drop of the count
-          const uint32_t w = s.off[d];
-          const uint32_t prev = (round & 1) ? (w & 0xFFFFu) : (w >> 16);
-          const uint32_t cur = (round & 1) ? (w >> 16) : (w & 0xFFFFu);
-          st[i] |= (prev - cur) << 13;
-          s.off[d] = (round & 1) ? (w & 0xFFFF0000u) : (w & 0xFFFFu);
-        }
-        left |= !(st[i] & SETTLED);
-      }
-      if (!__syncthreads_or(left)) break;
-      // next representatives: any unsettled key of the bucket
-#pragma unroll
-      for (int i = 0; i < IPT; ++i)
-        if (!(st[i] & SETTLED)) s.rep[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = (uint16_t)(st[i] & POS);
-      __syncthreads();
-    }
-    // survivors, in key order per thread; one scan gives both the survivor
-    // offsets (low half) and the group total (high half)
-    uint32_t n_groups = 0, n_keep = 0;
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      if (!(st[i] & HEAD)) continue;
-      const uint32_t c = (st[i] >> 13) & 0x1FFFu;
-      ++n_groups;
-      n_keep += c >= out.ci && c <= out.cx;
-    }
-    uint64_t tot2;
-    const uint64_t pre = block_excl_scan<uint64_t, THREADS>(((uint64_t)n_groups << 32) | n_keep,
-                                                            s.ws64, &tot2);
-    uint32_t kb = (uint32_t)pre;
-    const uint32_t ktot = (uint32_t)tot2;
-    if (tid == 0) {
-      s.base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
-      atomicAdd(out.n_distinct, tot2 >> 32);
-    }
-    __syncthreads();
-    const uint64_t base = s.base;
-    if (base + ktot > out.cap) {
-      if (tid == 0) atomicOr(err, ERR_CAPACITY);
-    } else if (n_keep) {
-#pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        if (!(st[i] & HEAD)) continue;
-        const uint32_t c = (st[i] >> 13) & 0x1FFFu;
-        if (c >= out.ci && c <= out.cx) {
-          out.keys[base + kb] = out.mixer.unmix(key[i]);
-          out.counts[base + kb] = c;
-          if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
-          ++kb;
-        }
-      }
-    }
+    });
   }
 }
 
@@ -1016,34 +1027,14 @@ __device__ bool big_sort(K *src_k, V *src_v, K *dst_k, V *dst_v, uint64_t n, int
   return in_dst;
 }
 
-// Count mode big tiles: sort (in place + scratch), then run-length count
-// chunk by chunk, carrying the open run across chunks.
 template <typename K, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
-big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, const uint32_t *n_big,
-                 K *scratch, unsigned long long *scratch_cursor, CountOut<K> out, uint32_t *err,
-                 K *sorted_out) {
-  using SM = BigSmem<K, NoVal, THREADS, IPT>;
+__device__ void big_count_range(K *src, K *dst, uint64_t n, int nbits, uint32_t group, const CountOut<K> &out,
+                                uint32_t *err, K *sorted_out, BigSmem<K, NoVal, THREADS, IPT> &sm) {
   constexpr int CH = THREADS * IPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SM &sm = *reinterpret_cast<SM *>(smem_raw);
-  const uint32_t nt = *plan.n_tiles;
-  const uint32_t nbig = *n_big;
-  for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
-  const uint32_t t = big_list[bi];
-  uint64_t st, en;
-  int nbits;
-  uint32_t group;
-  tile_range(plan, t, nt, &st, &en, &nbits, &group);
-  const uint64_t n = en - st;
-  if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
-  __syncthreads();
-  K *sc = scratch + sm.base;
-  const bool in_scratch = big_sort<K, NoVal, THREADS, IPT>(keys + st, (NoVal *)nullptr, sc,
-                                                           (NoVal *)nullptr, n, nbits, sm);
-  const K *a = in_scratch ? sc : keys + st;
+  const bool in_dst = big_sort<K, NoVal, THREADS, IPT>(src, (NoVal *)nullptr, dst, (NoVal *)nullptr, n, nbits, sm);
+  const K *a = in_dst ? dst : src;
   if (sorted_out)
-    for (uint64_t e = threadIdx.x; e < n; e += THREADS) sorted_out[st + e] = a[e];
+    for (uint64_t e = threadIdx.x; e < n; e += THREADS) sorted_out[e] = a[e];
   // heads: run starts; the run open at the end of a chunk continues in the next
   uint64_t open = 0;  // start of the open run (element 0 always starts one)
   uint32_t *ws = sm.ws;
@@ -1109,6 +1100,124 @@ big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, const uint32_
   }
   if (threadIdx.x == 0) atomicAdd(out.n_distinct, n_runs);
   __syncthreads();
+}
+
+// Count mode big tiles: sort (in place + scratch), then run-length count
+// chunk by chunk, carrying the open run across chunks.
+template <typename K, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+big_count_kernel(K *keys, TilePlan plan, const uint32_t *big_list, const uint32_t *n_big,
+                 K *scratch, unsigned long long *scratch_cursor, CountOut<K> out, uint32_t *err,
+                 K *sorted_out) {
+  using SM = BigSmem<K, NoVal, THREADS, IPT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t nt = *plan.n_tiles;
+  const uint32_t nbig = *n_big;
+  for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    const uint32_t t = big_list[bi];
+    uint64_t st, en;
+    int nbits;
+    uint32_t group;
+    tile_range(plan, t, nt, &st, &en, &nbits, &group);
+    const uint64_t n = en - st;
+    if (threadIdx.x == 0) sm.base = atomicAdd(scratch_cursor, (unsigned long long)n);
+    __syncthreads();
+    big_count_range<K, THREADS, IPT>(keys + st, scratch + sm.base, n, nbits, group, out, err,
+                                     sorted_out ? sorted_out + st : nullptr, sm);
+  }
+}
+
+// Count mode big tiles without a full sort: a big tile's keys are split by
+// bits kGroupBits .. kGroupBits+S (one more radix partition step, into global
+// scratch at the tile's own positions) into sub-buckets of about half a
+// tile, and each sub-bucket is counted like a tile.  A sub-bucket still
+// above a tile (copies of a few keys) is sorted through global memory.
+template <typename K, int THREADS, int IPT, int BIPT>
+struct BigGroupSmem {
+  union U {
+    TileGroupSmem<K, THREADS, IPT> g;
+    BigSmem<K, NoVal, THREADS, BIPT> b;
+  } u;
+  uint64_t lo[kGroupDigits + 1];  // sub-bucket starts (tile-relative)
+};
+
+template <typename K, int THREADS, int IPT, int BIPT>
+__global__ void __launch_bounds__(THREADS, 1)
+big_group_kernel(K *keys, TilePlan plan, const uint32_t *big_list, const uint32_t *n_big, K *scratch,
+                 CountOut<K> out, int key_bits, uint32_t *err) {
+  using SM = BigGroupSmem<K, THREADS, IPT, BIPT>;
+  constexpr int TILE = THREADS * IPT;
+  constexpr int DPT = kGroupDigits / THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &s = *reinterpret_cast<SM *>(smem_raw);
+  auto &g = s.u.g;
+  const uint32_t nt = *plan.n_tiles;
+  const uint32_t nbig = *n_big;
+  const int tid = threadIdx.x;
+  for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    const uint32_t t = big_list[bi];
+    uint64_t st, en;
+    int nbits;
+    uint32_t group;
+    tile_range(plan, t, nt, &st, &en, &nbits, &group);
+    const uint64_t n = en - st;
+    if (n >= (1ull << 32)) {  // positions below are 32-bit
+      if (tid == 0) atomicOr(err, ERR_CAPACITY);
+      continue;
+    }
+    int S = 0;
+    while (S < kGroupBits && (n >> S) > (uint64_t)TILE / 2) ++S;
+    const uint32_t smask = (1u << S) - 1u;
+    __syncthreads();  // the previous big tile is done with shared memory
+    for (int i = tid; i < kGroupDigits + 4; i += THREADS) g.off[i] = 0;
+    __syncthreads();
+    for (uint64_t e = tid; e < n; e += THREADS)
+      atomicAdd(&g.off[(uint32_t)((uint64_t)keys[st + e] >> kGroupBits) & smask], 1u);
+    __syncthreads();
+    {  // exclusive scan of the sub-digit counts
+      uint32_t c[DPT];
+#pragma unroll
+      for (int q = 0; q < DPT; q += 4) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(&g.off[DPT * tid + q]);
+        c[q] = v.x; c[q + 1] = v.y; c[q + 2] = v.z; c[q + 3] = v.w;
+      }
+      uint32_t sum = 0;
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) sum += c[q];
+      uint32_t tot;
+      uint32_t run = block_excl_scan<uint32_t, THREADS>(sum, g.ws, &tot);
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        const uint32_t x = c[q];
+        g.off[DPT * tid + q] = run;
+        s.lo[DPT * tid + q] = run;
+        run += x;
+      }
+      if (tid == 0) s.lo[kGroupDigits] = n;
+    }
+    __syncthreads();
+    for (uint64_t e = tid; e < n; e += THREADS) {
+      const K key = keys[st + e];
+      const uint32_t p = atomicAdd(&g.off[(uint32_t)((uint64_t)key >> kGroupBits) & smask], 1u);
+      scratch[st + p] = key;
+    }
+    __syncthreads();
+    for (uint32_t sb = 0; sb <= smask; ++sb) {
+      const uint64_t lo = s.lo[sb], hi = s.lo[sb + 1];
+      const uint64_t m = hi - lo;
+      if (m == 0) continue;
+      if (m <= (uint64_t)TILE) {
+        for (int e = tid; e < (int)m; e += THREADS) g.a[e] = scratch[st + lo + e];
+        __syncthreads();
+        group_core<K, THREADS, IPT>(g, (int)m, 0, group, out, err, []() {});
+      } else {
+        // the tile's own range in keys is free now: the sort's second buffer
+        big_count_range<K, THREADS, BIPT>(scratch + st + lo, keys + st + lo, m, key_bits, group, out, err,
+                                          nullptr, s.u.b);
+      }
+      __syncthreads();
+    }
   }
 }
 

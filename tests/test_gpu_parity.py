@@ -71,6 +71,16 @@ def test_mid_workload_scaled(k):
     assert_same(got, oracle_count(w.bases, w.offsets, k))
 
 
+def test_one_bin_takes_the_wide_digit_path():
+    # ~19 M k-mers in one bin need 14 digit bits, more than a unit
+    # histogram holds: the partition then reserves places per warp and digit
+    w = synth.mid(scale=0.008)
+    for k in (28, 40):
+        with kmc.Counter(k, m=w.m, n_bins=1) as c:
+            got = c.add(w.bases, w.offsets).count().result()
+        assert_same(got, oracle_count(w.bases, w.offsets, k))
+
+
 def test_large_workload_scaled_m9():
     w = synth.large(k=28, scale=0.002)
     for k in (28, 55):
