@@ -402,7 +402,7 @@ int sort_phase_x0(Handle &h) {
     // upper digits: generated keys -> super buckets (in ss.keys)
     sa.in = gen_keys;
     sa.out = keys;
-    kx0_sweep_kernel<K, 0><<<(unsigned)std::min<uint64_t>(h.sm_count, meta.n_units), SWEEP_THREADS,
+    kx0_sweep_kernel<K, 0><<<(unsigned)std::min<uint64_t>(2ull * h.sm_count, meta.n_units), SWEEP_THREADS,
                              sizeof(SweepSmem<K>), h.st>>>(sa);
     KMC_COUNT_LAUNCH();
     // lower digits: super buckets -> final buckets (back in keys_gen)

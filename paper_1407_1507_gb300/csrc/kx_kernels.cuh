@@ -264,14 +264,14 @@ kx0_scatter_kernel(KxArgs<K> a, const uint64_t *__restrict__ bucket_base,
 //    memory) for the lower digit, which puts every key in its final bucket,
 //    and stores the final bucket sizes.
 
-constexpr int SWEEP_THREADS = 1024;
+constexpr int SWEEP_THREADS = 512;
 constexpr int SWEEP_UPPER = 8;                  // bits of the upper digit
 constexpr int SWEEP_BITS_MAX = 2 * SWEEP_UPPER; // digit bits per bin this path supports
 
 template <typename K>
 struct SweepTraits {
   static constexpr int IPT = 128 / (int)sizeof(K);        // 16 u64 / 8 u128 keys per thread
-  static constexpr int TILE = SWEEP_THREADS * IPT;        // keys per tile (128 KB)
+  static constexpr int TILE = SWEEP_THREADS * IPT;        // keys per tile (64 KB)
 };
 
 struct PartUnit {
@@ -396,7 +396,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<K> &a, SweepSmem<K> &
   const int nd = 1 << (MODE == 0 ? (D < SWEEP_UPPER ? D : SWEEP_UPPER) : (D - (D < SWEEP_UPPER ? D : SWEEP_UPPER)));
   for (int i = tid; i < nd; i += SWEEP_THREADS) s.h[i] = 0;
   K key[IPT];
-  uint16_t rank[IPT];
+  uint32_t rank[IPT / 2];  // two 16-bit ranks per word
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
     const uint32_t e = tid + i * SWEEP_THREADS;
@@ -406,10 +406,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<K> &a, SweepSmem<K> &
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
     const uint32_t e = tid + i * SWEEP_THREADS;
+    uint32_t r = 0;
     if (e < n) {
       const uint32_t d = MODE == 0 ? upper_digit<K>(key[i], a.key_bits, D) : lower_digit<K>(key[i], a.key_bits, D);
-      rank[i] = (uint16_t)atomicAdd(&s.h[d], 1u);
+      r = atomicAdd(&s.h[d], 1u);
     }
+    if (i & 1) rank[i / 2] |= r << 16; else rank[i / 2] = r;
   }
   __syncthreads();
   // digit starts inside the tile (warp scans over the <= 256 counters) and
@@ -434,7 +436,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<K> &a, SweepSmem<K> &
     const uint32_t e = tid + i * SWEEP_THREADS;
     if (e < n) {
       const uint32_t d = MODE == 0 ? upper_digit<K>(key[i], a.key_bits, D) : lower_digit<K>(key[i], a.key_bits, D);
-      s.sorted[s.lstart[d] + rank[i]] = key[i];
+      s.sorted[s.lstart[d] + ((rank[i / 2] >> (16 * (i & 1))) & 0xFFFFu)] = key[i];
     }
   }
   __syncthreads();
@@ -450,7 +452,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<K> &a, SweepSmem<K> &
 // MODE 0: persistent CTAs over the bins' tiles (units).  MODE 1: one CTA per
 // super bucket.
 template <typename K, int MODE>
-__global__ void __launch_bounds__(SWEEP_THREADS, 1) kx0_sweep_kernel(SweepArgs<K> a) {
+__global__ void __launch_bounds__(SWEEP_THREADS, 2) kx0_sweep_kernel(SweepArgs<K> a) {
   constexpr int TILE = SweepTraits<K>::TILE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SweepSmem<K> &s = *reinterpret_cast<SweepSmem<K> *>(smem_raw);
