@@ -65,6 +65,21 @@ def dist_info():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """Largest value of x over the ranks (the slowest replica sets the step time)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all replicas processed over the (max) time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
 
@@ -214,11 +229,8 @@ def run_ours(args, rank, local_rank, world):
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = npos * world / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = job_rate(npos, world, ms)
 
     # roofline of the dominant kernel stage
     peaks, peak_kind = measured_peaks()
@@ -270,12 +282,8 @@ def run_ours(args, rank, local_rank, world):
             e2e_step()
         torch.cuda.synchronize(dev)
         barrier()
-        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": npos * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
+        e2e = {"value": job_rate(npos, world, e_ms), "unit": UNIT, "ms_per_step": round(e_ms, 3),
                "h2d_bytes_per_step": int(w.bases.size + w.offsets.size * 8),
                "d2h_bytes_per_step": int(nout * (8 * words + 4))}
     kmc.kmc_close(h)
