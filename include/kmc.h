@@ -74,7 +74,16 @@ typedef struct {
   uint64_t piece_bytes;/* reads are distributed in pieces of about this many
                           bytes (0 = 1 GiB); bounds the distribution scratch,
                           never changes the result                            */
-  uint64_t reserved[2];/* must be zero                                            */
+  uint64_t device_budget; /* device bytes for the bins and the sort buffers
+                          (0 = no limit).  With a limit, a piece whose bins
+                          would take the bins past half of it is moved to
+                          pinned host memory (async copy) and read from there
+                          over NVLink-C2C by the sort, and (x = 0) the bins
+                          are sorted in waves whose two key buffers take at
+                          most a quarter each; a single bin larger than a
+                          wave is still sorted whole.  Never changes the
+                          result.  Not applied to x > 0.                      */
+  uint64_t reserved[1];/* must be zero                                            */
 } kmc_params;
 
 /* Fills *p with the paper's defaults: k=25, m=7, 512 bins, x=KMC_AUTO,
@@ -104,6 +113,10 @@ typedef struct {
    * summed since kmc_open / kmc_reset, in the KMC_STAGE_* order below */
   float ms_stage[12];
   uint64_t n_launches;       /* kernels launched since kmc_open / kmc_reset    */
+  uint64_t spilled_bytes;    /* bin bytes moved to pinned host memory          */
+  uint32_t n_waves;          /* bin waves of the last kmc_count (1 without a
+                                device_budget)                                 */
+  uint32_t reserved_s;
 } kmc_stats;
 
 /* Stage indices of kmc_stats.ms_stage. */

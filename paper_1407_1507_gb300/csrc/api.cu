@@ -164,6 +164,11 @@ namespace {
 void free_piece(Piece *pc, cudaStream_t st) {
   dev_release(pc->index, st);
   dev_release(pc->words, st);
+  if (pc->host) {  // spilled bins: no kernel may still read them
+    cudaStreamSynchronize(st);
+    cudaFreeHost(pc->host);
+    pc->host = nullptr;
+  }
   dev_release(pc->rec_base, st);
   dev_release(pc->dbg_list, st);
   dev_release(pc->dbg_read, st);
@@ -180,7 +185,7 @@ void release_all(Handle &h) {
                     &h.ds.offs_dev[1], &h.ss.hist, &h.ss.bucket_base, &h.ss.cursor, &h.ss.flags,
                     &h.ss.flag_scan, &h.ss.tile_first, &h.ss.scan_tmp, &h.ss.keys, &h.ss.keys_gen,
                     &h.ss.sorted_keys, &h.ss.big_list, &h.ss.big_scratch, &h.ss.sv_keys,
-                    &h.ss.sv_counts, &h.ss.counters, &h.ss.o_hist, &h.ss.o_base, &h.ss.o_cursor,
+                    &h.ss.sv_counts, &h.ss.acc_keys, &h.ss.acc_counts, &h.ss.counters, &h.ss.o_hist, &h.ss.o_base, &h.ss.o_cursor,
                     &h.ss.o_flags, &h.ss.o_flag_scan, &h.ss.o_tile_first, &h.ss.o_scan_tmp,
                     &h.ss.o_big_list, &h.ss.o_big_k, &h.ss.o_big_v};
   for (DevBuf *b : bufs) dev_release(*b, h.st);
@@ -210,7 +215,7 @@ int validate(const kmc_params *p) {
   if (p->x != KMC_AUTO && p->x > 3) return KMC_EINVAL;
   if (p->cutoff_min > p->cutoff_max) return KMC_EINVAL;
   if (p->canonical != 1) return KMC_EINVAL;
-  if (p->reserved0 || p->reserved[0] || p->reserved[1]) return KMC_EINVAL;
+  if (p->reserved0 || p->reserved[0]) return KMC_EINVAL;
   if (p->debug_flags & ~(KMC_DEBUG_KEEP_SUPERKMERS | KMC_DEBUG_KEEP_KEYS | KMC_DEBUG_NARROW_SORT |
                          KMC_DEBUG_SIG_TILE))
     return KMC_EINVAL;
@@ -651,6 +656,7 @@ int kmc_reset(kmc_handle *kh) {
   h.n_out = 0;
   std::fill(h.bin_kmers.begin(), h.bin_kmers.end(), 0);
   h.stats = kmc_stats{};
+  h.dev_bin_bytes = 0;
   h.timer.clear();
   if (!h.map_user) h.map_ready = false;
   return KMC_OK;

@@ -214,15 +214,19 @@ struct SortMeta {
 
 // unit_keys > 0 asks for the generate + sweep path (x = 0, units of
 // unit_keys keys); it is taken when the bins' k-mers add up.
+// Only the bins of the wave [wb0, wb1) take part (the others are empty).
 int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta *m,
-               uint32_t unit_keys = 0) {
+               uint32_t unit_keys = 0, uint32_t wb0 = 0, uint32_t wb1 = ~0u) {
   SortScratch &ss = h.ss;
   const uint32_t B = h.p.n_bins;
+  if (wb1 > B) wb1 = B;
+  std::vector<uint64_t> bk(B, 0);
+  for (uint32_t b = wb0; b < wb1; ++b) bk[b] = h.bin_kmers[b];
   std::vector<uint32_t> gbase(B + 1);
   std::vector<uint8_t> gD(B);
   uint64_t NB = 0;
   for (uint32_t b = 0; b < B; ++b) {
-    gD[b] = (uint8_t)digits_for((uint64_t)(h.bin_kmers[b] * keys_per_kmer), key_bits, tile);
+    gD[b] = (uint8_t)digits_for((uint64_t)(bk[b] * keys_per_kmer), key_bits, tile);
     // the two sweeps place at most SWEEP_BITS_MAX digit bits; bigger bins
     // get bigger buckets, which the big-tile pass splits further
     if (unit_keys) gD[b] = (uint8_t)std::min<int>(gD[b], SWEEP_BITS_MAX);
@@ -237,12 +241,12 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   bool gen = unit_keys > 0;
   if (gen) {
     for (uint32_t b = 0; b < B; ++b) {
-      kbase[b + 1] = kbase[b] + h.bin_kmers[b];
+      kbase[b + 1] = kbase[b] + bk[b];
       sbase[b + 1] = sbase[b] + (1u << std::min<int>(gD[b], SWEEP_UPPER));
-      for (uint64_t o = 0; o < h.bin_kmers[b]; o += unit_keys)
-        units.push_back({kbase[b] + o, (uint32_t)std::min<uint64_t>(unit_keys, h.bin_kmers[b] - o), b});
+      for (uint64_t o = 0; o < bk[b]; o += unit_keys)
+        units.push_back({kbase[b] + o, (uint32_t)std::min<uint64_t>(unit_keys, bk[b] - o), b});
     }
-    if (kbase[B] != h.stats.n_kmer_positions) gen = false;
+    if (wb0 == 0 && wb1 == B && kbase[B] != h.stats.n_kmer_positions) gen = false;
     if (!gen) units.clear();
   }
   const uint32_t n_super = gen ? sbase[B] : 0;
@@ -250,9 +254,9 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   std::vector<PieceDesc> pds;
   for (size_t p = 0; p < h.pieces.size(); ++p) {
     Piece *pc = h.pieces[p];
-    pds.push_back({static_cast<const uint64_t *>(pc->index.p), static_cast<const uint64_t *>(pc->words.p)});
+    pds.push_back({pc->d_index, pc->d_words});
     const std::vector<uint64_t> &rb = pc->rec_base_host;
-    for (uint32_t b = 0; b < B; ++b)
+    for (uint32_t b = wb0; b < wb1; ++b)
       for (uint64_t r = rb[b]; r < rb[b + 1]; r += KX_RECORDS_PER_CHUNK)
         chunks.push_back({r, (uint32_t)std::min<uint64_t>(KX_RECORDS_PER_CHUNK, rb[b + 1] - r),
                           (uint32_t)p, b, 0});
@@ -335,16 +339,16 @@ int order_result(Handle &h, DevBuf &sv_k, DevBuf &sv_c, uint64_t n_sv, int k) {
   return check_device_error(h);
 }
 
+// One wave: the bins [wb0, wb1) with n_keys k-mers, counted into
+// (ss.sv_keys, ss.sv_counts); *n_sv receives the survivors.
 template <typename K, int IPT>
-int sort_phase_x0(Handle &h) {
+int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_t *n_sv_out) {
   SortScratch &ss = h.ss;
   constexpr int TILE = CNT_THREADS * IPT;
   const int k = (int)h.p.k;
   const int key_bits = 2 * k;
-  const uint64_t n_keys = h.stats.n_kmer_positions;
-  h.stats.n_sorted_keys = n_keys;
   SortMeta meta;
-  int rc = build_meta(h, key_bits, TILE, 1.0, &meta, SweepTraits<K>::TILE);
+  int rc = build_meta(h, key_bits, TILE, 1.0, &meta, SweepTraits<K>::TILE, wb0, wb1);
   if (rc) return rc;
   KxArgs<K> a;
   a.n_chunks_dyn = nullptr;
@@ -455,17 +459,74 @@ int sort_phase_x0(Handle &h) {
     if (dev_ensure(ss.sorted_keys, (n_keys + 1) * sizeof(K), h.st)) return KMC_ENOMEM;
     sorted_out = as<K>(ss.sorted_keys);
   }
-  uint64_t n_sv = 0;
-  h.stats.n_big_tiles = 0;
   rc = count_tiles<K, IPT>(h, plan, n_keys, keys, a.mixer, h.p.cutoff_min, h.p.cutoff_max,
-                           ss.sv_keys, ss.sv_counts, &n_sv, sorted_out, scratch);
+                           ss.sv_keys, ss.sv_counts, n_sv_out, sorted_out, scratch);
   if (rc) return rc;
   uint32_t nt = 0;
   KMC_CUDA_TRY(cudaMemcpyAsync(&nt, n_tiles_dev, 4, cudaMemcpyDeviceToHost, h.st));
   KMC_CUDA_TRY(cudaStreamSynchronize(h.st));
-  h.stats.n_tiles = nt;
+  h.stats.n_tiles += nt;
+  return KMC_OK;
+}
+
+// x = 0.  Without a device budget the bins form one wave; with one, waves
+// of consecutive bins whose keys fit a quarter of the budget per key buffer
+// are sorted one after the other and their survivors gathered.
+template <typename K, int IPT>
+int sort_phase_x0(Handle &h) {
+  SortScratch &ss = h.ss;
+  constexpr int TILE = CNT_THREADS * IPT;
+  const uint32_t B = h.p.n_bins;
+  h.stats.n_sorted_keys = h.stats.n_kmer_positions;
+  h.stats.n_big_tiles = 0;
+  h.stats.n_tiles = 0;
   h.stats.x_used = 0;
-  return order_result<K>(h, ss.sv_keys, ss.sv_counts, n_sv, k);
+  std::vector<uint32_t> cut{0};
+  std::vector<uint64_t> wkeys;
+  {
+    const uint64_t cap = h.p.device_budget ? std::max<uint64_t>(1, h.p.device_budget / 4 / sizeof(K))
+                                           : ~0ull;
+    uint64_t acc = 0;
+    for (uint32_t b = 0; b < B; ++b) {
+      if (b > cut.back() && acc + h.bin_kmers[b] > cap) {
+        cut.push_back(b);
+        wkeys.push_back(acc);
+        acc = 0;
+      }
+      acc += h.bin_kmers[b];
+    }
+    cut.push_back(B);
+    wkeys.push_back(acc);
+  }
+  const size_t n_waves = wkeys.size();
+  h.stats.n_waves = (uint32_t)n_waves;
+  if (n_waves == 1) {
+    uint64_t n_sv = 0;
+    int rc = sort_wave_x0<K, IPT>(h, 0, B, wkeys[0], &n_sv);
+    if (rc) return rc;
+    return order_result<K>(h, ss.sv_keys, ss.sv_counts, n_sv, (int)h.p.k);
+  }
+  // gather the waves' survivors
+  const uint64_t ci = h.p.cutoff_min ? h.p.cutoff_min : 1;
+  const uint64_t acc_cap = h.stats.n_kmer_positions / ci + n_waves * (TILE + 1) + 1;
+  if (dev_ensure(ss.acc_keys, acc_cap * sizeof(K), h.st) || dev_ensure(ss.acc_counts, acc_cap * 4, h.st))
+    return KMC_ENOMEM;
+  uint64_t total = 0, distinct = 0;
+  for (size_t w = 0; w < n_waves; ++w) {
+    if (!wkeys[w]) continue;
+    uint64_t n_sv = 0;
+    int rc = sort_wave_x0<K, IPT>(h, cut[w], cut[w + 1], wkeys[w], &n_sv);
+    if (rc) return rc;
+    distinct += h.stats.n_distinct;
+    if (total + n_sv > acc_cap) return KMC_ENOMEM;
+    KMC_CUDA_TRY(cudaMemcpyAsync(as<K>(ss.acc_keys) + total, ss.sv_keys.p, n_sv * sizeof(K),
+                                 cudaMemcpyDeviceToDevice, h.st));
+    KMC_CUDA_TRY(cudaMemcpyAsync(as<uint32_t>(ss.acc_counts) + total, ss.sv_counts.p, n_sv * 4,
+                                 cudaMemcpyDeviceToDevice, h.st));
+    total += n_sv;
+  }
+  h.stats.n_distinct = distinct;
+  return order_result<K>(h, ss.acc_keys, ss.acc_counts, total, (int)h.p.k);
 }
 
 constexpr int WCNT_IPT64 = 16;
@@ -691,6 +752,7 @@ uint32_t resolve_x(uint32_t k, uint32_t x) {
 int sort_phase(Handle &h) {
   const uint32_t k = h.p.k;
   const int x = (int)resolve_x(k, h.p.x);
+  h.stats.n_waves = 1;
   if (x == 0) {
     if (k <= 32) return sort_phase_x0<uint64_t, CNT_IPT64>(h);
     return sort_phase_x0<u128, CNT_IPT128>(h);

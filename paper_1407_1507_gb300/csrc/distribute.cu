@@ -245,6 +245,32 @@ int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_
       KMC_CUDA_TRY(cudaGetLastError());
     }
   }
+  pc->d_index = static_cast<const uint64_t *>(pc->index.p);
+  pc->d_words = static_cast<const uint64_t *>(pc->words.p);
+  const uint64_t bytes = (n_rec + 1 + n_words + STREAM_PAD_WORDS) * 8;
+  if (h.p.device_budget && h.dev_bin_bytes + bytes > h.p.device_budget / 2) {
+    // over the device share of the budget: the bins go to pinned host memory
+    // (copied after the scatter on this stream), the sort reads them there
+    void *host = nullptr;
+    if (cudaHostAlloc(&host, bytes, cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return KMC_ENOMEM;
+    }
+    pc->host = host;
+    uint64_t *hi = static_cast<uint64_t *>(host), *hw = hi + n_rec + 1;
+    KMC_CUDA_TRY(cudaMemcpyAsync(hi, pc->index.p, (n_rec + 1) * 8, cudaMemcpyDeviceToHost, h.st));
+    KMC_CUDA_TRY(cudaMemcpyAsync(hw, pc->words.p, (n_words + STREAM_PAD_WORDS) * 8, cudaMemcpyDeviceToHost,
+                                 h.st));
+    void *dp = nullptr;
+    KMC_CUDA_TRY(cudaHostGetDevicePointer(&dp, host, 0));
+    pc->d_index = static_cast<const uint64_t *>(dp);
+    pc->d_words = static_cast<const uint64_t *>(dp) + n_rec + 1;
+    dev_release(pc->index, h.st);  // stream-ordered: after the copies
+    dev_release(pc->words, h.st);
+    h.stats.spilled_bytes += bytes;
+  } else {
+    h.dev_bin_bytes += bytes;
+  }
   h.stats.n_superkmers += n_rec;
   h.stats.n_kmer_positions += pc->n_kmers;
   h.stats.bin_bytes += (n_words + n_rec) * 8;

@@ -29,6 +29,10 @@ inline T *as(DevBuf &b) { return static_cast<T *>(b.p); }
 struct Piece {
   DevBuf index;        // uint64[n_records]
   DevBuf words;        // uint64[n_words + pad]
+  // where kernels read the bins: index/words above, or (spilled) a pinned
+  // host copy, mapped into the device's address space
+  const uint64_t *d_index = nullptr, *d_words = nullptr;
+  void *host = nullptr;  // the pinned host copy (index, then words)
   DevBuf rec_base;     // uint64[B+1]: first record of each bin
   std::vector<uint64_t> rec_base_host;
   uint64_t n_records = 0;
@@ -63,6 +67,7 @@ struct SortScratch {
   DevBuf hist, bucket_base, cursor, flags, flag_scan, tile_first, scan_tmp;
   DevBuf keys, keys_gen, sorted_keys, big_list, big_scratch;
   DevBuf sv_keys, sv_counts;  // survivors before global order
+  DevBuf acc_keys, acc_counts;  // survivors of all waves (sort in waves)
   DevBuf counters;
   // global-order pass
   DevBuf o_hist, o_base, o_cursor, o_flags, o_flag_scan, o_tile_first, o_scan_tmp, o_big_list,
@@ -115,6 +120,7 @@ struct Handle {
   // statistics
   kmc_stats stats{};
   std::vector<uint64_t> bin_kmers;   // k-mer positions per bin (all pieces)
+  uint64_t dev_bin_bytes = 0;        // bin bytes of the pieces kept on the device
   cudaEvent_t ev[8] = {};
   StageTimer timer;
 };

@@ -38,7 +38,8 @@ class kmc_params(ctypes.Structure):
         ("x", ctypes.c_uint32), ("cutoff_min", ctypes.c_uint64), ("cutoff_max", ctypes.c_uint64),
         ("canonical", ctypes.c_uint32), ("device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
         ("debug_flags", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
-        ("piece_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2),
+        ("piece_bytes", ctypes.c_uint64), ("device_budget", ctypes.c_uint64),
+        ("reserved", ctypes.c_uint64 * 1),
     ]
 
 
@@ -53,10 +54,11 @@ class kmc_stats(ctypes.Structure):
         ("ms_distribute", ctypes.c_float), ("ms_sort", ctypes.c_float),
         ("ms_order", ctypes.c_float), ("ms_total", ctypes.c_float),
         ("ms_stage", ctypes.c_float * 12), ("n_launches", ctypes.c_uint64),
+        ("spilled_bytes", ctypes.c_uint64), ("n_waves", ctypes.c_uint32), ("reserved_s", ctypes.c_uint32),
     ]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved_s"}
         d["ms_stage"] = {STAGES[i]: float(self.ms_stage[i]) for i in range(len(STAGES))}
         return d
 
@@ -417,7 +419,7 @@ def kmc_server_close(s):
 # ----------------------------------------------------------- convenience
 
 def make_params(k, m=7, n_bins=512, x=KMC_AUTO, cutoff_min=2, cutoff_max=10**9, device=0,
-                stream=None, debug_flags=0, piece_bytes=0) -> kmc_params:
+                stream=None, debug_flags=0, piece_bytes=0, device_budget=0) -> kmc_params:
     p = kmc_default_params()
     p.k, p.m, p.n_bins = k, m, n_bins
     p.x = KMC_AUTO if x is None else x
@@ -426,6 +428,7 @@ def make_params(k, m=7, n_bins=512, x=KMC_AUTO, cutoff_min=2, cutoff_max=10**9, 
     p.cuda_stream = stream
     p.debug_flags = debug_flags
     p.piece_bytes = piece_bytes
+    p.device_budget = device_budget
     return p
 
 

@@ -81,6 +81,26 @@ def test_one_bin_takes_the_wide_digit_path():
         assert_same(got, oracle_count(w.bases, w.offsets, k))
 
 
+@pytest.mark.parametrize("k", [28, 40])
+def test_device_budget_spills_bins_and_sorts_in_waves(k):
+    # a budget of a quarter of the bins' bytes: most pieces' bins go to
+    # pinned host memory, and the bins are sorted in many waves
+    w = synth.mid(scale=0.002)
+    want = oracle_count(w.bases, w.offsets, k)
+    with kmc.Counter(k, m=7, n_bins=64, piece_bytes=1 << 20) as c:
+        c.add(w.bases, w.offsets)
+        bin_bytes = c.stats()["bin_bytes"]
+        assert_same(c.count().result(), want)
+        assert c.stats()["n_waves"] == 1 and c.stats()["spilled_bytes"] == 0
+    with kmc.Counter(k, m=7, n_bins=64, piece_bytes=1 << 20, device_budget=bin_bytes // 4) as c:
+        c.add(w.bases, w.offsets)
+        st = c.stats()
+        assert st["spilled_bytes"] > bin_bytes // 2
+        assert_same(c.count().result(), want)
+        assert c.stats()["n_waves"] > 4
+        assert_same(c.count().result(), want)  # recount from the spilled bins
+
+
 def test_large_workload_scaled_m9():
     w = synth.large(k=28, scale=0.002)
     for k in (28, 55):
