@@ -439,18 +439,22 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   }
   if (small_bins && a.list)
     for (int i = L; i < hb; i += SIG2_LANES) h_rec[i] = h_words[i] = h_kmers[i] = 0;
-  if (L == 0) {
-    // start of the read holding position max(LBm, 0)
-    uint64_t lo = a.r0, hi = a.r1;
-    if (a.n_reads_dyn && *a.n_reads_dyn < hi) hi = *a.n_reads_dyn;
+  if (L < 32) {
+    // last read start before position LBm: the read-start mask read
+    // backwards, 32 words (2,048 positions) per step
     int64_t rs = 0;
-    const int64_t q = LBm > 0 ? LBm : 0;
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi) / 2;
-      const int64_t sp = (int64_t)(a.offsets[mid] - a.byte_start) + a.mis;
-      if (sp <= q) { rs = sp; lo = mid + 1; } else hi = mid;
+    for (int64_t wb = mw0 - 1; wb >= 0; wb -= 32) {
+      const int64_t wq = wb - L;
+      const uint64_t x = (wq >= 0 && (uint64_t)wq < a.n_mwords) ? a.smask[wq] : 0ull;
+      const unsigned hit = __ballot_sync(FULL, x != 0);
+      if (hit) {
+        const int src = __ffs(hit) - 1;  // the highest word with a start
+        const uint64_t xs = __shfl_sync(FULL, x, src);
+        rs = (wb - src) * 64 + 63 - (__ffsll((long long)xs) - 1);
+        break;
+      }
     }
-    rs0 = rs;
+    if (L == 0) rs0 = rs;
   }
   __syncthreads();
   if (L < 32) {
@@ -473,22 +477,33 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
       if (tot > carry) carry = tot;
     }
   }
-  // phase 1: m-mer values of the lane's block and their prefix minima
+  // phase 1: m-mer values of the lane's block and their prefix minima; the
+  // 2-bit codes stream out of a register word, refilled every 32 bases
   const int64_t p0 = B0 + (int64_t)L * w;               // >= B0 >= LB, LBm
   {
     const uint32_t mmask = SENT - 1u;
+    const uint32_t bit0 = (uint32_t)(2 * (p0 - LB));
+    int wi = (int)(bit0 >> 6);
+    uint64_t cur = pk[wi] << (bit0 & 63);
+    int rem = 32 - (int)((bit0 & 63) >> 1);
     uint32_t fw = 0, rc = 0;
-    uint64_t bit = (uint64_t)(2 * (p0 - LB));
-    for (int q = 0; q < m - 1; ++q, bit += 2) {
-      const uint32_t c = (uint32_t)get_bits(pk, bit, 2);
+    const int rsh = 2 * m - 2;
+    for (int q = 0; q < m - 1; ++q) {
+      if (rem == 0) { cur = pk[++wi]; rem = 32; }
+      const uint32_t c = (uint32_t)(cur >> 62);
+      cur <<= 2;
+      --rem;
       fw = ((fw << 2) | c) & mmask;
-      rc = (rc >> 2) | ((3u - c) << (2 * m - 2));
+      rc = (rc >> 2) | ((3u - c) << rsh);
     }
     uint32_t pm = 0xFFFFFFFFu;
-    for (int j = 0; j < w; ++j, bit += 2) {
-      const uint32_t c = (uint32_t)get_bits(pk, bit, 2);
+    for (int j = 0; j < w; ++j) {
+      if (rem == 0) { cur = pk[++wi]; rem = 32; }
+      const uint32_t c = (uint32_t)(cur >> 62);
+      cur <<= 2;
+      --rem;
       fw = ((fw << 2) | c) & mmask;
-      rc = (rc >> 2) | ((3u - c) << (2 * m - 2));
+      rc = (rc >> 2) | ((3u - c) << rsh);
       const uint32_t cn = fw < rc ? fw : rc;                 // canonical m-mer (Sect. 2.1)
       const uint32_t v = mmer_allowed(cn, m) ? cn : SENT;     // Sect. 2.2 filter
       V[L * stride + j] = v;
@@ -508,42 +523,64 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
     }
   }
   __syncthreads();
-  // phase 3: validity, cut rule, breaks and owned starts of the lane's block
-  const int64_t own_end = T0 + own;
+  // phase 3: validity, cut rule, breaks and owned starts of the lane's block.
+  // Positions are local (lp = position - LBm).  A k-mer at lp is valid when
+  // base lp is a base and the next "bad" position (invalid base or read
+  // start) after lp is at least lp + k away; both masks stream out of
+  // register words, and the next bad position is searched only once passed.
   uint64_t brk_mask = 0, start_mask = 0;
   if (L < SIG2_LANES - 1) {
-    // a k-mer at pos is valid when its k bases are bases and no read starts
-    // inside it (after pos)
-    auto valid_at = [&](uint64_t lp) -> bool {
+    auto valid_at = [&](uint64_t lp) -> bool {  // direct test (one position)
       if ((iv[lp >> 6] >> (63 - (lp & 63))) & 1ull) return false;
       return k == 1 || get_bits(cm, lp + 1, k - 1) == 0ull;
     };
+    const uint32_t lp0 = (uint32_t)(p0 - LBm);
     // lane 0's first position precedes the owned range: no start flag needed
     bool pv = false;
     uint32_t psig = 0;
-    const uint64_t lp0 = (uint64_t)(p0 - LBm);
     if (L > 0) {
       pv = valid_at(lp0 - 1);
       psig = V[(L - 1) * stride + (w - 1)];
     }
-    // last read start strictly before p0
-    int64_t rs;
+    // last read start strictly before lp0 (local; may be negative)
+    int32_t rs;
     {
       const int wi = (int)(lp0 >> 6);
-      const unsigned o = (unsigned)(lp0 & 63);
+      const unsigned o = lp0 & 63;
       const uint64_t x = o ? (sm[wi] & (~0ull << (64 - o))) : 0ull;
-      rs = x ? LBm + (int64_t)wi * 64 + 64 - __ffsll((long long)x) : lastw[wi];
+      rs = x ? wi * 64 + 64 - __ffsll((long long)x) : (int32_t)(lastw[wi] - LBm);
     }
+    // first bad position > q (local), searched word by word
+    auto next_bad = [&](uint32_t q) -> uint32_t {
+      uint32_t t = q + 1;
+      int wq = (int)(t >> 6);
+      uint64_t x = cm[wq] << (t & 63);
+      if (x) return t + __clzll((long long)x);
+      while (++wq < SIG2_MWORDS) {
+        x = cm[wq];
+        if (x) return (uint32_t)wq * 64 + __clzll((long long)x);
+      }
+      return 0xFFFFFFFFu;
+    };
+    uint32_t nb = next_bad(lp0);
+    int mw = (int)(lp0 >> 6), mrem = 64 - (int)(lp0 & 63);
+    uint64_t ivc = iv[mw] << (lp0 & 63), smc = sm[mw] << (lp0 & 63);
+    const uint32_t own_lo = (uint32_t)(T0 - LBm), own_hi = own_lo + (uint32_t)own;
     for (int j = 0; j < w; ++j) {
-      const int64_t pos = p0 + j;
-      const uint64_t lp = lp0 + j;
-      if ((sm[lp >> 6] >> (63 - (lp & 63))) & 1ull) rs = pos;
-      const bool v = pos >= 0 && valid_at(lp);
+      const uint32_t lp = lp0 + j;
+      if (mrem == 0) { ++mw; ivc = iv[mw]; smc = sm[mw]; mrem = 64; }
+      const bool inv = (ivc >> 63) != 0, start = (smc >> 63) != 0;
+      ivc <<= 1;
+      smc <<= 1;
+      --mrem;
+      if (start) rs = (int32_t)lp;
+      if (nb <= lp) nb = next_bad(lp);
+      const bool v = !inv && (k == 1 || nb >= lp + (uint32_t)k);
       const uint32_t sg = V[L * stride + j];
-      const bool cut = v && (((uint32_t)(pos - rs) & (kSuperkmerCap - 1)) == 0);
+      const bool cut = v && ((((uint32_t)((int32_t)lp - rs)) & (kSuperkmerCap - 1)) == 0);
       const bool st = v && (!pv || sg != psig || cut);
       if (!v || st) brk_mask |= 1ull << j;
-      if (st && pos >= T0 && pos < own_end) start_mask |= 1ull << j;
+      if (st && lp >= own_lo && lp < own_hi) start_mask |= 1ull << j;
       pv = v;
       psig = sg;
     }
