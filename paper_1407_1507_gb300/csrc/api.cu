@@ -183,7 +183,7 @@ void release_all(Handle &h) {
                     &h.ds.starts, &h.ds.list, &h.ds.counters, &h.ds.hist, &h.ds.scan_tmp,
                     &h.ds.bin_scan, &h.ds.stage_dev[0], &h.ds.stage_dev[1], &h.ds.offs_dev[0],
                     &h.ds.offs_dev[1], &h.ss.hist, &h.ss.bucket_base, &h.ss.cursor, &h.ss.flags,
-                    &h.ss.flag_scan, &h.ss.tile_first, &h.ss.scan_tmp, &h.ss.keys, &h.ss.keys_gen,
+                    &h.ss.flag_scan, &h.ss.tile_first, &h.ss.scan_tmp, &h.ss.keys, &h.ss.keys_gen, &h.ss.tile_desc,
                     &h.ss.sorted_keys, &h.ss.big_list, &h.ss.big_scratch, &h.ss.sv_keys,
                     &h.ss.sv_counts, &h.ss.acc_keys, &h.ss.acc_counts, &h.ss.counters, &h.ss.o_hist, &h.ss.o_base, &h.ss.o_cursor,
                     &h.ss.o_flags, &h.ss.o_flag_scan, &h.ss.o_tile_first, &h.ss.o_scan_tmp,

@@ -146,7 +146,7 @@ struct BatchEngine {
   DevBuf in, offs, set_starts, dyn, err, map;
   DevBuf packed, inval, starts, list, hist3, rec_base, word_base, cursors, index, words;
   DevBuf chunk_cnt, chunk_base, chunks, group_D, group_sz, group_base64, group_base, pieces;
-  DevBuf hist, bucket_base, flags, fscan, tfirst, scan_tmp, keys, sv_keys, sv_counts, sv_slots,
+  DevBuf hist, bucket_base, flags, fscan, tfirst, tdesc, scan_tmp, keys, sv_keys, sv_counts, sv_slots,
       big_list, big_scratch, counters;
   DevBuf okeys, okeys2, ovals2, o_hist, o_base, o_flags, o_fscan, o_tfirst, o_grp, o_big_list,
       o_big_k, o_big_v, o_counters, res_kmers, set_hist, set_base;
@@ -167,7 +167,7 @@ struct BatchEngine {
     DevBuf *bufs[] = {&in, &offs, &set_starts, &dyn, &err, &map, &packed, &inval, &starts, &list,
                       &hist3, &rec_base, &word_base, &cursors, &index, &words, &chunk_cnt,
                       &chunk_base, &chunks, &group_D, &group_sz, &group_base64, &group_base,
-                      &pieces, &hist, &bucket_base, &flags, &fscan, &tfirst, &scan_tmp, &keys,
+                      &pieces, &hist, &bucket_base, &flags, &fscan, &tfirst, &tdesc, &scan_tmp, &keys,
                       &sv_keys, &sv_counts, &sv_slots, &big_list, &big_scratch, &counters, &okeys,
                       &okeys2, &ovals2, &o_hist, &o_base, &o_flags, &o_fscan, &o_tfirst, &o_grp,
                       &o_big_list, &o_big_k, &o_big_v, &o_counters, &res_kmers, &set_hist, &set_base};
@@ -217,6 +217,7 @@ struct BatchEngine {
         E(group_base64, ((size_t)B_total + 1) * 8) || E(group_base, ((size_t)B_total + 1) * 4) ||
         E(pieces, 64) || E(hist, NB_max * 4) || E(bucket_base, (NB_max + 1) * 8) ||
         E(flags, NB_max * 4) || E(fscan, (NB_max + 1) * 8) || E(tfirst, NB_max * 4 + 16) ||
+        E(tdesc, (NB_max + 1) * sizeof(TileDesc)) ||
         E(scan_tmp, scan_tmp_words(std::max<uint64_t>(NB_max, std::max<uint64_t>(B_total, ond))) * 8) ||
         E(keys, (list_cap + 2) * 8) || E(sv_keys, sv_cap * 8) || E(sv_counts, sv_cap * 4) ||
         E(sv_slots, sv_cap * 4) || E(big_list, (list_cap / (tile + 1) + 2) * 4) ||
@@ -311,10 +312,14 @@ int BatchEngine::count_stage(const TilePlan &plan, const Mixer<uint64_t> &mixer)
   out.bins_per_slot = tune.bins;
   const int occ = occ_count;
   const uint32_t big_cap = (uint32_t)(list_cap / (256ull * IPT + 1) + 2);
+  TilePlan gplan = plan;
+  gplan.desc = as<TileDesc>(tdesc);
+  tile_desc_kernel<<<(unsigned)std::min<uint64_t>((plan.NB + 255) / 256, 4096), 256, 0, st>>>(plan,
+                                                                                           as<TileDesc>(tdesc));
+  KMC_COUNT_LAUNCH();
   tile_group_kernel<K, GRP_THREADS, GIPT><<<(unsigned)std::max(1, occ) * sm_count, GRP_THREADS, sizeof(GSM),
                                             st>>>(
-      as<K>(keys), plan, c32 + 0, out, as<uint32_t>(big_list), c32 + 1, c64 + 2, big_cap,
-      as<uint32_t>(err));
+      as<K>(keys), gplan, c32 + 0, out, as<uint32_t>(big_list), c32 + 1, c64 + 2, big_cap, as<uint32_t>(err));
   KMC_COUNT_LAUNCH();
   big_count_kernel<K, B_THREADS, B_BIG_IPT><<<sm_count, B_THREADS, sizeof(BSM), st>>>(
       as<K>(keys), plan, as<uint32_t>(big_list), c32 + 1, as<K>(big_scratch), c64 + 3, out,

@@ -88,10 +88,17 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
   if (grouped) {
     KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, tile_group_kernel<K, GRP_THREADS, GIPT>, GRP_THREADS, sizeof(GSM)));
+    // tile ranges first: a CTA then takes a tile with one load
+    if (dev_ensure(ss.tile_desc, ((size_t)plan.NB + 1) * sizeof(TileDesc), h.st)) return KMC_ENOMEM;
+    TilePlan gplan = plan;
+    gplan.desc = as<TileDesc>(ss.tile_desc);
     StageScope sc(h, KMC_STAGE_TILE_SORT);
+    tile_desc_kernel<<<(unsigned)std::min<uint64_t>((plan.NB + 255) / 256, 4096), 256, 0, h.st>>>(
+        plan, as<TileDesc>(ss.tile_desc));
+    KMC_COUNT_LAUNCH();
     tile_group_kernel<K, GRP_THREADS, GIPT><<<(unsigned)std::max(1, occ) * h.sm_count, GRP_THREADS,
                                               sizeof(GSM), h.st>>>(
-        keys, plan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
+        keys, gplan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
         as<uint32_t>(h.err)); KMC_COUNT_LAUNCH();
   } else {
     KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(

@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(SIG_THREADS) sig_kernel(SigArgs a) {
 // starting one position before the k-mer starts it owns and extending
 // kSuperkmerCap past them (a super k-mer never spans more).
 
-constexpr int SIG2_LANES = 256;
+constexpr int SIG2_LANES = 128;
 constexpr int SIG2_MAXW = 64;
 constexpr int SIG2_MWORDS = (SIG2_LANES * SIG2_MAXW + 256) / 64 + 4;  // mask words staged
 constexpr int SIG2_PWORDS = 2 * SIG2_MWORDS;                            // packed words staged

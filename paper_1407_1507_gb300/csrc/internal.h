@@ -65,7 +65,7 @@ struct DistScratch {
 // Per-call scratch of the sorting phase.
 struct SortScratch {
   DevBuf hist, bucket_base, cursor, flags, flag_scan, tile_first, scan_tmp;
-  DevBuf keys, keys_gen, sorted_keys, big_list, big_scratch;
+  DevBuf keys, keys_gen, sorted_keys, big_list, big_scratch, tile_desc;
   DevBuf sv_keys, sv_counts;  // survivors before global order
   DevBuf acc_keys, acc_counts;  // survivors of all waves (sort in waves)
   DevBuf counters;

@@ -68,8 +68,11 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
   constexpr int TILE = PAIR_THREADS * PAIR_IPT;
   SortScratch &ss = h.ss;
   if (n <= 1) return KMC_OK;
+  // many small buckets (about TILE/64 keys each): the top bits of canonical
+  // k-mers are skewed, and the tile plan packs small buckets back together,
+  // while a bucket above a tile would take the slow path
   int D = 0;
-  while (D < PAIR_MAX_D && D < key_bits && (n >> D) > (uint64_t)TILE / 4) ++D;
+  while (D < PAIR_MAX_D && D < key_bits && (n >> D) > (uint64_t)TILE / 64) ++D;
   const uint32_t ND = 1u << D;
   if (dev_ensure(ss.o_hist, (size_t)ND * 4 + 4, h.st) || dev_ensure(ss.o_base, ((size_t)ND + 1) * 8, h.st) ||
       dev_ensure(ss.o_flags, (size_t)ND * 4 + 4, h.st) ||

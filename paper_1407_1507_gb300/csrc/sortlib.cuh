@@ -194,6 +194,14 @@ __host__ __device__ __forceinline__ int tile_sort_bits(int key_bits, int D, uint
 // bucket i (exclusive scan of the counts; bucket_base[NB] = total).
 // tile_first[t] = flattened index of the first bucket of tile t; a tile
 // never crosses a group boundary and ends where tile t+1 begins.
+// Key range and group of one tile, precomputed so that a CTA takes its next
+// tile with one load.
+struct TileDesc {
+  uint64_t st;     // first key
+  uint32_t n;      // keys
+  uint32_t group;  // group (bin) of the tile
+};
+
 struct TilePlan {
   const uint64_t *bucket_base;  // [NB + 1]
   const uint32_t *tile_first;   // [n_tiles]
@@ -203,6 +211,7 @@ struct TilePlan {
   uint32_t n_groups;
   uint32_t NB;                  // total buckets
   int key_bits;
+  const TileDesc *desc = nullptr;  // optional: [n_tiles] ranges (tile_desc_kernel)
 };
 
 // Group holding bucket i (largest g with group_base[g] <= i).
@@ -228,6 +237,19 @@ __device__ __forceinline__ void tile_range(const TilePlan &p, uint32_t t, uint32
   const uint32_t d0 = i - p.group_base[g], d1 = j - 1 - p.group_base[g];
   *nbits = tile_sort_bits(p.key_bits, p.group_D[g], d0, d1);
   if (group) *group = g;
+}
+
+// desc[t] for every tile t < *plan.n_tiles (grid-stride).
+static __global__ void tile_desc_kernel(TilePlan plan, TileDesc *desc) {
+  const uint32_t nt = *plan.n_tiles;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    uint64_t st, en;
+    int nbits;
+    uint32_t group;
+    tile_range(plan, t, nt, &st, &en, &nbits, &group);
+    const uint64_t n = en - st;
+    desc[t] = {st, n > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)n, group};
+  }
 }
 
 // Optional bijective mix of the keys (2^bits values onto themselves): the
@@ -505,7 +527,7 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
 // count.  Rounds = most values in one bucket; heavy keys cost no serial work.
 // The tile's keys are staged in shared memory by a bulk copy started while
 // the previous tile is still being counted.
-constexpr int kGroupBits = 12;
+constexpr int kGroupBits = 11;
 constexpr int kGroupDigits = 1 << kGroupBits;
 
 template <typename K, int THREADS, int IPT>
@@ -518,6 +540,9 @@ struct TileGroupSmem {
   // scatter: per digit, keys left unsettled by the last two rounds (16-bit halves)
   uint32_t off[kGroupDigits + 4];
   uint16_t rep[kGroupDigits];     // position in b of each bucket's current representative
+  // keys left after the first round: position (bits 0-11), group count
+  // (bits 12-24), settled (bit 30), group head (bit 31)
+  uint32_t wl[THREADS * IPT];
   uint32_t ws[THREADS / 32 + 1];
   uint64_t ws64[THREADS / 32 + 1];
   uint64_t bar;                   // mbarrier of the bulk copies
@@ -539,25 +564,21 @@ __device__ void group_fetch(const K *keys, const TilePlan &plan, uint32_t nt, ui
       s.t_next = nt;
       return;
     }
-    uint64_t st, en;
-    int nbits;
-    uint32_t group;
-    tile_range(plan, t, nt, &st, &en, &nbits, &group);
-    const uint64_t n = en - st;
-    if (n == 0) continue;
-    if (n > (uint64_t)SM::TILE) {
-      push_big(t, n, big_list, n_big, big_keys, big_cap, err);
+    const TileDesc d = plan.desc[t];
+    if (d.n == 0) continue;
+    if (d.n > (uint32_t)SM::TILE) {
+      push_big(t, d.n, big_list, n_big, big_keys, big_cap, err);
       continue;
     }
-    // copy the 16-byte aligned cover of keys[st, en) (the key buffers keep
-    // 16 bytes of slack past their last key)
-    const uintptr_t src = reinterpret_cast<uintptr_t>(keys + st);
+    // copy the 16-byte aligned cover of keys[st, st + n) (the key buffers
+    // keep 16 bytes of slack past their last key)
+    const uintptr_t src = reinterpret_cast<uintptr_t>(keys + d.st);
     const uintptr_t src0 = src & ~(uintptr_t)15;
-    const uint32_t bytes = (uint32_t)((src + n * sizeof(K) - src0 + 15) & ~(uintptr_t)15);
+    const uint32_t bytes = (uint32_t)((src + (uint64_t)d.n * sizeof(K) - src0 + 15) & ~(uintptr_t)15);
     s.t_next = t;
-    s.n_next = (uint32_t)n;
+    s.n_next = d.n;
     s.lead_next = (uint32_t)((src - src0) / sizeof(K));
-    s.group_next = group;
+    s.group_next = d.group;
     fence_proxy_async_smem();
     bulk_load(s.a, reinterpret_cast<const void *>(src0), bytes, &s.bar);
     return;
@@ -643,38 +664,74 @@ __device__ __forceinline__ void group_core(TileGroupSmem<K, THREADS, IPT> &s, in
   for (int i = 0; i < IPT; ++i)
     if (bsize[i]) s.off[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = bsize[i];
   __syncthreads();
-  // rounds: count j of unsettled keys sits in half j & 1 of the digit's word
-  for (uint32_t round = 1;; ++round) {
-    const uint32_t inc = (round & 1) ? 0x10000u : 1u;
+  // rounds: count j of unsettled keys sits in half j & 1 of the digit's
+  // word.  Round 1 (each bucket's first key represents it) runs on the keys
+  // in registers; the few keys it leaves go to a work list for the rest.
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      if (st[i] & SETTLED) continue;
-      const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
-      const uint32_t r = s.rep[d];
-      if (s.b[r] == key[i]) st[i] |= SETTLED | (r == (st[i] & POS) ? HEAD : 0u);
-      else atomicAdd(&s.off[d], inc);
-    }
-    __syncthreads();
-    bool left = false;
+  for (int i = 0; i < IPT; ++i) {
+    if (st[i] & SETTLED) continue;
+    const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
+    const uint32_t r = s.rep[d];
+    if (s.b[r] == key[i]) st[i] |= SETTLED | (r == (st[i] & POS) ? HEAD : 0u);
+    else atomicAdd(&s.off[d], 0x10000u);
+  }
+  __syncthreads();
+  uint32_t left = 0;
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
+  for (int i = 0; i < IPT; ++i) {
+    if (st[i] & HEAD) {
       const uint32_t d = (uint32_t)(uint64_t)key[i] & (kGroupDigits - 1);
-      if ((st[i] & HEAD) && ((st[i] >> 13) & 0x1FFFu) == 0) {
-        // this round's representative: its group is the drop of the count
-        const uint32_t w = s.off[d];
-        const uint32_t prev = (round & 1) ? (w & 0xFFFFu) : (w >> 16);
-        const uint32_t cur = (round & 1) ? (w >> 16) : (w & 0xFFFFu);
-        st[i] |= (prev - cur) << 13;
-        s.off[d] = (round & 1) ? (w & 0xFFFF0000u) : (w & 0xFFFFu);
-      }
-      left |= !(st[i] & SETTLED);
+      const uint32_t w = s.off[d];
+      st[i] |= ((w & 0xFFFFu) - (w >> 16)) << 13;
+      s.off[d] = w & 0xFFFF0000u;
     }
-    if (!__syncthreads_or(left)) break;
-    // next representatives: any unsettled key of the bucket
+    left += !(st[i] & SETTLED);
+  }
+  uint32_t n_wl;
+  uint32_t wo = block_excl_scan<uint32_t, THREADS>(left, s.ws, &n_wl);
+  if (left) {
 #pragma unroll
     for (int i = 0; i < IPT; ++i)
-      if (!(st[i] & SETTLED)) s.rep[(uint32_t)(uint64_t)key[i] & (kGroupDigits - 1)] = (uint16_t)(st[i] & POS);
+      if (!(st[i] & SETTLED)) s.wl[wo++] = st[i] & POS;
+  }
+  constexpr uint32_t WPOS = 0xFFFu;
+  if (n_wl) {
     __syncthreads();
+    for (uint32_t round = 2;; ++round) {
+      // representatives: any unsettled key of the bucket
+      for (uint32_t e = tid; e < n_wl; e += THREADS) {
+        const uint32_t x = s.wl[e];
+        if (!(x & SETTLED)) s.rep[(uint32_t)(uint64_t)s.b[x & WPOS] & (kGroupDigits - 1)] = (uint16_t)(x & WPOS);
+      }
+      __syncthreads();
+      const uint32_t inc = (round & 1) ? 0x10000u : 1u;
+      for (uint32_t e = tid; e < n_wl; e += THREADS) {
+        const uint32_t x = s.wl[e];
+        if (x & SETTLED) continue;
+        const uint32_t p = x & WPOS;
+        const K kk = s.b[p];
+        const uint32_t d = (uint32_t)(uint64_t)kk & (kGroupDigits - 1);
+        const uint32_t r = s.rep[d];
+        if (s.b[r] == kk) s.wl[e] = x | SETTLED | (r == p ? HEAD : 0u);
+        else atomicAdd(&s.off[d], inc);
+      }
+      __syncthreads();
+      bool more = false;
+      for (uint32_t e = tid; e < n_wl; e += THREADS) {
+        const uint32_t x = s.wl[e];
+        if ((x & HEAD) && ((x >> 12) & 0x1FFFu) == 0) {
+          // this round's representative: its group is the drop of the count
+          const uint32_t d = (uint32_t)(uint64_t)s.b[x & WPOS] & (kGroupDigits - 1);
+          const uint32_t w = s.off[d];
+          const uint32_t prev = (round & 1) ? (w & 0xFFFFu) : (w >> 16);
+          const uint32_t cur = (round & 1) ? (w >> 16) : (w & 0xFFFFu);
+          s.wl[e] = x | ((prev - cur) << 12);
+          s.off[d] = (round & 1) ? (w & 0xFFFF0000u) : (w & 0xFFFFu);
+        }
+        more |= !(x & SETTLED);
+      }
+      if (!__syncthreads_or(more)) break;
+    }
   }
   // survivors, in key order per thread; one scan gives both the survivor
   // offsets (low half) and the group total (high half)
@@ -683,6 +740,13 @@ __device__ __forceinline__ void group_core(TileGroupSmem<K, THREADS, IPT> &s, in
   for (int i = 0; i < IPT; ++i) {
     if (!(st[i] & HEAD)) continue;
     const uint32_t c = (st[i] >> 13) & 0x1FFFu;
+    ++n_groups;
+    n_keep += c >= out.ci && c <= out.cx;
+  }
+  for (uint32_t e = tid; e < n_wl; e += THREADS) {
+    const uint32_t x = s.wl[e];
+    if (!(x & HEAD)) continue;
+    const uint32_t c = (x >> 12) & 0x1FFFu;
     ++n_groups;
     n_keep += c >= out.ci && c <= out.cx;
   }
@@ -711,14 +775,26 @@ __device__ __forceinline__ void group_core(TileGroupSmem<K, THREADS, IPT> &s, in
         ++kb;
       }
     }
+    for (uint32_t e = tid; e < n_wl; e += THREADS) {
+      const uint32_t x = s.wl[e];
+      if (!(x & HEAD)) continue;
+      const uint32_t c = (x >> 12) & 0x1FFFu;
+      if (c >= out.ci && c <= out.cx) {
+        out.keys[base + kb] = out.mixer.unmix(s.b[x & WPOS]);
+        out.counts[base + kb] = c;
+        if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
+        ++kb;
+      }
+    }
   }
 }
 
 template <typename K, int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS, 2)
 tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<K> out,
-                  uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys,
-                  uint32_t big_cap, uint32_t *err) {
+                  uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys, uint32_t big_cap,
+                  uint32_t *err) {
+  // plan.desc is required; tiles are claimed from *work (zero at launch)
   using SM = TileGroupSmem<K, THREADS, IPT>;
   static_assert(offsetof(SM, off) % 16 == 0 && offsetof(SM, a) == 0, "16-byte aligned arrays");
   extern __shared__ __align__(16) unsigned char smem_raw[];
