@@ -376,6 +376,8 @@ constexpr int SIG2_MAXW = 64;
 constexpr int SIG2_MWORDS = (SIG2_LANES * SIG2_MAXW + 256) / 64 + 4;  // mask words staged
 constexpr int SIG2_PWORDS = 2 * SIG2_MWORDS;                            // packed words staged
 static_assert((kSuperkmerCap & (kSuperkmerCap - 1)) == 0, "cut test uses a mask");
+// a CTA's per-bin counters are packed in 21-bit fields
+static_assert((SIG2_LANES - 1) * SIG2_MAXW * 8 < (1 << 21), "per-CTA counts fit 21 bits");
 
 __host__ __device__ inline int sig2_own(int k, int m) {
   const int w = k - m + 1;
@@ -389,7 +391,7 @@ __host__ __device__ inline int sig2_hist_bins(uint32_t n_bins) {
 }
 inline size_t sig2_smem_bytes(int k, int m, uint32_t n_bins) {
   return (size_t)SIG2_PWORDS * 8 + 4 * (size_t)SIG2_MWORDS * 8 + (size_t)SIG2_LANES * 8 +
-         2 * (size_t)SIG2_LANES * sig2_stride(k, m) * 4 + 3 * (size_t)sig2_hist_bins(n_bins) * 4;
+         2 * (size_t)SIG2_LANES * sig2_stride(k, m) * 4 + (size_t)sig2_hist_bins(n_bins) * 8;
 }
 // The lane-block form pays off once a block holds several positions.
 inline bool sig2_applies(int k, int m) { return k - m + 1 >= 8 && k - m + 1 <= SIG2_MAXW; }
@@ -414,9 +416,8 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   int64_t *fbrk = lastw + SIG2_MWORDS;                  // first break of each lane's block
   uint32_t *V = reinterpret_cast<uint32_t *>(fbrk + SIG2_LANES);   // values, then signatures
   uint32_t *P = V + SIG2_LANES * stride;                           // prefix minima
-  uint32_t *h_rec = P + SIG2_LANES * stride;
-  uint32_t *h_words = h_rec + hb;
-  uint32_t *h_kmers = h_words + hb;
+  // per-bin records | words << 21 | k-mers << 42 of this CTA (fields < 2^21)
+  unsigned long long *hpk = reinterpret_cast<unsigned long long *>(P + SIG2_LANES * stride);
   __shared__ uint32_t ws[SIG2_LANES / 32 + 1];
   __shared__ int64_t rs0;
   __shared__ unsigned long long out_base;
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
     cm[i] = x | y;
   }
   if (small_bins && a.list)
-    for (int i = L; i < hb; i += SIG2_LANES) h_rec[i] = h_words[i] = h_kmers[i] = 0;
+    for (int i = L; i < hb; i += SIG2_LANES) hpk[i] = 0;
   if (L < 32) {
     // last read start before position LBm: the read-start mask read
     // backwards, 32 words (2,048 positions) per step
@@ -550,40 +551,56 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
       const uint64_t x = o ? (sm[wi] & (~0ull << (64 - o))) : 0ull;
       rs = x ? wi * 64 + 64 - __ffsll((long long)x) : (int32_t)(lastw[wi] - LBm);
     }
-    // first bad position > q (local), searched word by word
-    auto next_bad = [&](uint32_t q) -> uint32_t {
-      uint32_t t = q + 1;
-      int wq = (int)(t >> 6);
-      uint64_t x = cm[wq] << (t & 63);
-      if (x) return t + __clzll((long long)x);
-      while (++wq < SIG2_MWORDS) {
-        x = cm[wq];
-        if (x) return (uint32_t)wq * 64 + __clzll((long long)x);
+    // Bit-parallel over the lane's w positions, MSB first (bit 63 - j is
+    // position lp0 + j).  valid: base j is a base and no bad position (an
+    // invalid base or a read start) lies in (j, j + k): a sliding OR of
+    // width k-1 over the 128-bit window of bad bits from lp0 + 1, built by
+    // doubling.
+    const uint64_t wmask = w >= 64 ? ~0ull : ~(~0ull >> w);  // the top w bits
+    const uint64_t inv_b = get_bits(iv, lp0, 64);
+    uint64_t valid = ~inv_b;
+    if (k > 1) {
+      uint64_t H = get_bits(cm, (uint64_t)lp0 + 1, 64), Lo = get_bits(cm, (uint64_t)lp0 + 65, 64);
+      int width = 1;
+      while (2 * width <= k - 1) {  // R[i] = OR of the window [i, i + 2 width)
+        H |= (H << width) | (Lo >> (64 - width));
+        Lo |= Lo << width;
+        width *= 2;
       }
-      return 0xFFFFFFFFu;
-    };
-    uint32_t nb = next_bad(lp0);
-    int mw = (int)(lp0 >> 6), mrem = 64 - (int)(lp0 & 63);
-    uint64_t ivc = iv[mw] << (lp0 & 63), smc = sm[mw] << (lp0 & 63);
-    const uint32_t own_lo = (uint32_t)(T0 - LBm), own_hi = own_lo + (uint32_t)own;
-    for (int j = 0; j < w; ++j) {
-      const uint32_t lp = lp0 + j;
-      if (mrem == 0) { ++mw; ivc = iv[mw]; smc = sm[mw]; mrem = 64; }
-      const bool inv = (ivc >> 63) != 0, start = (smc >> 63) != 0;
-      ivc <<= 1;
-      smc <<= 1;
-      --mrem;
-      if (start) rs = (int32_t)lp;
-      if (nb <= lp) nb = next_bad(lp);
-      const bool v = !inv && (k == 1 || nb >= lp + (uint32_t)k);
-      const uint32_t sg = V[L * stride + j];
-      const bool cut = v && ((((uint32_t)((int32_t)lp - rs)) & (kSuperkmerCap - 1)) == 0);
-      const bool st = v && (!pv || sg != psig || cut);
-      if (!v || st) brk_mask |= 1ull << j;
-      if (st && lp >= own_lo && lp < own_hi) start_mask |= 1ull << j;
-      pv = v;
-      psig = sg;
+      const int rest = k - 1 - width;  // then [i, i + k - 1) = R[i] | R[i + rest]
+      if (rest > 0) H |= (H << rest) | (Lo >> (64 - rest));
+      valid &= ~H;
     }
+    valid &= wmask;
+    // cuts: every read start, and the multiples of kSuperkmerCap from the
+    // read start before the window up to the first start in it
+    const uint64_t starts = get_bits(sm, lp0, 64) & wmask;
+    uint64_t cut = starts;
+    {
+      const uint32_t d = (uint32_t)((int32_t)lp0 - rs);
+      const uint32_t c = (kSuperkmerCap - (d & (kSuperkmerCap - 1))) & (kSuperkmerCap - 1);
+      const uint32_t f = starts ? (uint32_t)__clzll((long long)starts) : 64u;
+      if (c < f && c < (uint32_t)w) cut |= 1ull << (63 - c);
+    }
+    // signature changes
+    uint64_t chg = 0;
+    {
+      uint32_t prev = psig;
+      for (int j = 0; j < w; ++j) {
+        const uint32_t sg = V[L * stride + j];
+        chg |= (uint64_t)(sg != prev) << (63 - j);
+        prev = sg;
+      }
+    }
+    const uint64_t prev_valid = (valid >> 1) | (pv ? 1ull << 63 : 0ull);
+    const uint64_t st = valid & (~prev_valid | chg | cut);
+    const uint64_t brk = (~valid | st) & wmask;
+    // owned starts: local positions [own_lo, own_hi)
+    const int32_t olo = (int32_t)(T0 - LBm) - (int32_t)lp0, ohi = olo + own;
+    const int j0 = olo < 0 ? 0 : (olo > 64 ? 64 : olo), j1 = ohi < 0 ? 0 : (ohi > 64 ? 64 : ohi);
+    const uint64_t own_m = (j1 > j0) ? ((j1 - j0 >= 64 ? ~0ull : ((1ull << (j1 - j0)) - 1)) << (64 - j1)) : 0ull;
+    brk_mask = __brevll(brk);
+    start_mask = __brevll(st & own_m);
   }
   fbrk[L] = brk_mask ? p0 + (__ffsll((long long)brk_mask) - 1) : INT64_MAX;
   __syncthreads();
@@ -627,9 +644,7 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
     const uint32_t bin = slot_of(a.set_starts, a.n_slots, (uint64_t)pos) * a.bins_per_slot + a.map[g];
     const uint32_t nw = (2 * (n + k - 1) + 63) / 64;
     if (small_bins) {
-      atomicAdd(&h_rec[bin], 1u);
-      atomicAdd(&h_words[bin], nw);
-      atomicAdd(&h_kmers[bin], n);
+      atomicAdd(&hpk[bin], 1ull | ((unsigned long long)nw << 21) | ((unsigned long long)n << 42));
     } else {
       atomicAdd(&a.bin_rec[bin], 1ull);
       atomicAdd(&a.bin_words[bin], (unsigned long long)nw);
@@ -639,10 +654,11 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   if (small_bins && a.list) {
     __syncthreads();
     for (int i = L; i < hb; i += SIG2_LANES) {
-      if (h_rec[i]) {
-        atomicAdd(&a.bin_rec[i], (unsigned long long)h_rec[i]);
-        atomicAdd(&a.bin_words[i], (unsigned long long)h_words[i]);
-        atomicAdd(&a.bin_kmers[i], (unsigned long long)h_kmers[i]);
+      const unsigned long long v = hpk[i];
+      if (v) {
+        atomicAdd(&a.bin_rec[i], v & 0x1FFFFFull);
+        atomicAdd(&a.bin_words[i], (v >> 21) & 0x1FFFFFull);
+        atomicAdd(&a.bin_kmers[i], v >> 42);
       }
     }
   }
