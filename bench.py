@@ -173,8 +173,8 @@ def stage_bytes(st, k):
         "pack": nb * 1.0 + nb / 4 + nb / 4,            # ASCII in; 2-bit codes + 2 masks out
         "signature": nb / 4 + nb / 4 + 8 * nrec,        # codes + masks in; records out
         "bin_scatter": 8 * nrec + binb / 2 + binb,      # records + bases in; bins out
-        "kx_count": binb,                               # bins in
-        "kx_scatter": binb + kw * npos,                 # bins in; keys out
+        "kx_count": binb + kw * npos,                   # bins in; keys out (built once)
+        "kx_scatter": 4 * kw * npos,                    # two sweeps: keys in and out, each
         "tile_sort": kw * npos + (kw + 4) * nout,       # keys in; survivors out
         "order": 2 * (kw + 4) * nout,                   # survivors in and out
     }

@@ -255,7 +255,7 @@ struct BatchEngine {
     return KMC_OK;
   }
 
-  int occ_count = 1, occ_order = 1;
+  int occ_count = 1, occ_order = 1, occ_hash = 1;
   template <int IPT>
   int prepare_count() {
     constexpr int GIPT = B_THREADS * IPT / GRP_THREADS;
@@ -267,6 +267,12 @@ struct BatchEngine {
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BSM)));
     KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ_count, tile_group_kernel<uint64_t, GRP_THREADS, GIPT>, GRP_THREADS, sizeof(GSM)));
+    constexpr int HIPT = B_THREADS * IPT / HASH_THREADS;
+    using HSM = TileHashSmem<HASH_THREADS, HIPT>;
+    KMC_CUDA_TRY(cudaFuncSetAttribute(tile_hash_kernel<HASH_THREADS, HIPT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HSM)));
+    KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ_hash, tile_hash_kernel<HASH_THREADS, HIPT>, HASH_THREADS, sizeof(HSM)));
     return KMC_OK;
   }
   template <typename KO>
@@ -317,9 +323,16 @@ int BatchEngine::count_stage(const TilePlan &plan, const Mixer<uint64_t> &mixer)
   tile_desc_kernel<<<(unsigned)std::min<uint64_t>((plan.NB + 255) / 256, 4096), 256, 0, st>>>(plan,
                                                                                            as<TileDesc>(tdesc));
   KMC_COUNT_LAUNCH();
-  tile_group_kernel<K, GRP_THREADS, GIPT><<<(unsigned)std::max(1, occ) * sm_count, GRP_THREADS, sizeof(GSM),
-                                            st>>>(
-      as<K>(keys), gplan, c32 + 0, out, as<uint32_t>(big_list), c32 + 1, c64 + 2, big_cap, as<uint32_t>(err));
+  if (2 * (int)p.k <= 62) {  // keys below 2^62: hashed tiles
+    constexpr int HIPT = B_THREADS * IPT / HASH_THREADS;
+    tile_hash_kernel<HASH_THREADS, HIPT><<<(unsigned)std::max(1, occ_hash) * sm_count, HASH_THREADS,
+                                           sizeof(TileHashSmem<HASH_THREADS, HIPT>), st>>>(
+        as<K>(keys), gplan, c32 + 0, out, as<uint32_t>(big_list), c32 + 1, c64 + 2, big_cap, as<uint32_t>(err));
+  } else {
+    tile_group_kernel<K, GRP_THREADS, GIPT><<<(unsigned)std::max(1, occ) * sm_count, GRP_THREADS, sizeof(GSM),
+                                              st>>>(
+        as<K>(keys), gplan, c32 + 0, out, as<uint32_t>(big_list), c32 + 1, c64 + 2, big_cap, as<uint32_t>(err));
+  }
   KMC_COUNT_LAUNCH();
   big_count_kernel<K, B_THREADS, B_BIG_IPT><<<sm_count, B_THREADS, sizeof(BSM), st>>>(
       as<K>(keys), plan, as<uint32_t>(big_list), c32 + 1, as<K>(big_scratch), c64 + 3, out,

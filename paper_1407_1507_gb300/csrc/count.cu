@@ -85,7 +85,32 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
     attr = true;
   }
   int occ = 0;
-  if (grouped) {
+  // 64-bit keys below 2^62 are counted through a hash table per tile
+  constexpr int HTHREADS = HASH_THREADS, HIPT = TILE / HTHREADS;
+  using HSM = TileHashSmem<HTHREADS, HIPT>;
+  const bool hashed = grouped && sizeof(K) == 8 && plan.key_bits <= 62;
+  if constexpr (sizeof(K) == 8) if (hashed) {
+    static bool hattr = false;
+    if (!hattr) {
+      KMC_CUDA_TRY(cudaFuncSetAttribute(tile_hash_kernel<HTHREADS, HIPT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HSM)));
+      hattr = true;
+    }
+    if (dev_ensure(ss.tile_desc, ((size_t)plan.NB + 1) * sizeof(TileDesc), h.st)) return KMC_ENOMEM;
+    TilePlan gplan = plan;
+    gplan.desc = as<TileDesc>(ss.tile_desc);
+    StageScope sc(h, KMC_STAGE_TILE_SORT);
+    tile_desc_kernel<<<(unsigned)std::min<uint64_t>((plan.NB + 255) / 256, 4096), 256, 0, h.st>>>(
+        plan, as<TileDesc>(ss.tile_desc));
+    KMC_COUNT_LAUNCH();
+    int hocc = 0;
+    KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hocc, tile_hash_kernel<HTHREADS, HIPT>,
+                                                               HTHREADS, sizeof(HSM)));
+    tile_hash_kernel<HTHREADS, HIPT><<<(unsigned)std::max(1, hocc) * h.sm_count, HTHREADS, sizeof(HSM), h.st>>>(
+        keys, gplan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
+        as<uint32_t>(h.err)); KMC_COUNT_LAUNCH();
+  }
+  if (!hashed && grouped) {
     KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, tile_group_kernel<K, GRP_THREADS, GIPT>, GRP_THREADS, sizeof(GSM)));
     // tile ranges first: a CTA then takes a tile with one load
@@ -100,7 +125,7 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
                                               sizeof(GSM), h.st>>>(
         keys, gplan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
         as<uint32_t>(h.err)); KMC_COUNT_LAUNCH();
-  } else {
+  } else if (!hashed) {
     KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &occ, tile_count_kernel<K, CNT_THREADS, IPT>, CNT_THREADS, sizeof(SM)));
     StageScope sc(h, KMC_STAGE_TILE_SORT);

@@ -553,11 +553,12 @@ struct TileGroupSmem {
 
 // Thread 0: takes tiles until one fits (bigger ones go to the big list,
 // empty ones are skipped), starts its bulk copy and records it.
-template <typename K, int THREADS, int IPT>
-__device__ void group_fetch(const K *keys, const TilePlan &plan, uint32_t nt, uint32_t *work,
-                            TileGroupSmem<K, THREADS, IPT> &s, uint32_t *big_list, uint32_t *n_big,
-                            unsigned long long *big_keys, uint32_t big_cap, uint32_t *err) {
-  using SM = TileGroupSmem<K, THREADS, IPT>;
+// SM: shared-memory layout with a (copy target), bar, t_next, n_next,
+// lead_next, group_next and the tile capacity TILE.
+template <typename K, typename SM>
+__device__ void tile_fetch(const K *keys, const TilePlan &plan, uint32_t nt, uint32_t *work, SM &s,
+                           uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys,
+                           uint32_t big_cap, uint32_t *err) {
   for (;;) {
     const uint32_t t = atomicAdd(work, 1u);
     if (t >= nt) {
@@ -803,7 +804,7 @@ tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&s.bar, 1);
-    group_fetch<K, THREADS, IPT>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
+    tile_fetch<K>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
   }
   __syncthreads();
   uint32_t parity = 0;
@@ -811,8 +812,9 @@ tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
     if (s.t_next >= nt) break;
     const int n = (int)s.n_next, lead = (int)s.lead_next;
     const uint32_t group = s.group_next;
-    const bool ok = mbar_wait(&s.bar, parity);
-    // (this barrier also ends the previous tile: all threads are past its output)
+    // thread 0 waits for the copy; the barrier passes its result (and the
+    // copied data) on to the others, and ends the previous tile
+    const bool ok = tid != 0 || mbar_wait(&s.bar, parity);
     if (!__syncthreads_and(ok)) {
       // the copy did not land in time: report, give it one more bounded
       // wait so that no copy is left in flight, and stop
@@ -824,8 +826,165 @@ tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
     }
     parity ^= 1u;
     group_core<K, THREADS, IPT>(s, n, lead, group, out, err, [&]() {
-      group_fetch<K, THREADS, IPT>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
+      tile_fetch<K>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
     });
+  }
+}
+
+// ------------------------------------------------------- hashed count tiles
+// Count mode for 64-bit keys below 2^62 (k <= 31): the keys of a tile go
+// into an open-addressing table in shared memory (twice the tile's size,
+// linear probing from the key's low bits, one 64-bit CAS to claim a slot and
+// one atomic add to count), and the occupied slots are the tile's distinct
+// keys.  Same input and output as tile_group_kernel with far fewer steps per
+// key; copies of one key meet at one slot whatever their number.  Tiles are
+// staged by bulk copies into a ring of HASH_STAGES buffers, so that several
+// copies per SM are in flight (one per CTA does not cover HBM latency).
+constexpr int HASH_STAGES = 1;
+constexpr int HASH_THREADS = 512;
+constexpr int HASH_SLOTS = 5120;  // 1.25 slots per key of a 4096-key tile
+
+template <int THREADS, int IPT>
+struct TileHashSmem {
+  static constexpr int TILE = THREADS * IPT;
+  static constexpr int SLOTS = HASH_SLOTS;
+  uint64_t a[HASH_STAGES][TILE + 4];  // staged keys (bulk copy targets)
+  unsigned long long tk[SLOTS];       // slot keys (kHashEmpty when free)
+  uint32_t tc[SLOTS];                 // slot counts
+  uint64_t ws64[THREADS / 32 + 1];
+  uint64_t bar[HASH_STAGES];
+  unsigned long long base;
+  struct Stage {
+    uint32_t t, n, lead, group;       // t = number of tiles: no tile in this stage
+  } st[HASH_STAGES];
+};
+constexpr unsigned long long kHashEmpty = ~0ull;
+
+// Thread 0: claims the next tile that fits (bigger ones go to the big list,
+// empty ones are skipped) and starts its copy into stage b.
+template <int THREADS, int IPT>
+__device__ void hash_issue(const uint64_t *keys, const TilePlan &plan, uint32_t nt, uint32_t *work,
+                           TileHashSmem<THREADS, IPT> &s, int b, uint32_t *big_list, uint32_t *n_big,
+                           unsigned long long *big_keys, uint32_t big_cap, uint32_t *err) {
+  using SM = TileHashSmem<THREADS, IPT>;
+  for (;;) {
+    const uint32_t t = atomicAdd(work, 1u);
+    if (t >= nt) {
+      s.st[b].t = nt;
+      return;
+    }
+    const TileDesc d = plan.desc[t];
+    if (d.n == 0) continue;
+    if (d.n > (uint32_t)SM::TILE) {
+      push_big(t, d.n, big_list, n_big, big_keys, big_cap, err);
+      continue;
+    }
+    // the 16-byte aligned cover of keys[st, st + n) (16 bytes of slack exist)
+    const uintptr_t src = reinterpret_cast<uintptr_t>(keys + d.st);
+    const uintptr_t src0 = src & ~(uintptr_t)15;
+    const uint32_t bytes = (uint32_t)((src + (uint64_t)d.n * 8 - src0 + 15) & ~(uintptr_t)15);
+    s.st[b] = {t, d.n, (uint32_t)((src - src0) / 8), d.group};
+    fence_proxy_async_smem();
+    bulk_load(s.a[b], reinterpret_cast<const void *>(src0), bytes, &s.bar[b]);
+    return;
+  }
+}
+
+template <int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS > 1 ? 2 : 1)
+tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<uint64_t> out,
+                 uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys, uint32_t big_cap,
+                 uint32_t *err) {
+  using SM = TileHashSmem<THREADS, IPT>;
+  constexpr int SPT = SM::SLOTS / THREADS;  // slots per thread
+  static_assert(SM::SLOTS % THREADS == 0 && SM::SLOTS > SM::TILE && offsetof(SM, a) == 0 &&
+                ((SM::TILE + 4) * 8) % 16 == 0, "layout");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &s = *reinterpret_cast<SM *>(smem_raw);
+  const uint32_t nt = *plan.n_tiles;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int b = 0; b < HASH_STAGES; ++b) mbar_init(&s.bar[b], 1);
+    for (int b = 0; b < HASH_STAGES; ++b)
+      hash_issue<THREADS, IPT>(keys, plan, nt, work, s, b, big_list, n_big, big_keys, big_cap, err);
+  }
+  __syncthreads();
+  uint32_t parity = 0;  // bit b: phase parity of stage b's barrier
+  for (int b = 0;; b = (b + 1 == HASH_STAGES) ? 0 : b + 1) {
+    const typename SM::Stage cur = s.st[b];
+    if (cur.t >= nt) break;  // stages are filled in order: nothing after this either
+    const int n = (int)cur.n, lead = (int)cur.lead;
+    // thread 0 waits for the copy; the barrier passes its result (and the
+    // copied data) on to the others, and ends the previous tile
+    const bool ok = tid != 0 || mbar_wait(&s.bar[b], (parity >> b) & 1u);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+        for (int q = 0; q < HASH_STAGES; ++q)
+          if (s.st[q].t < nt) mbar_wait(&s.bar[q], (parity >> q) & 1u);
+      }
+      return;
+    }
+    parity ^= 1u << b;
+    // clear the table (thread t owns slots t, t + THREADS, ...) and take the tile's keys
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      s.tk[q * THREADS + tid] = kHashEmpty;
+      s.tc[q * THREADS + tid] = 0;
+    }
+    uint64_t key[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int e = tid + i * THREADS;
+      key[i] = e < n ? s.a[b][lead + e] : kHashEmpty;
+    }
+    __syncthreads();  // stage b consumed, table clear
+    if (tid == 0) hash_issue<THREADS, IPT>(keys, plan, nt, work, s, b, big_list, n_big, big_keys, big_cap, err);
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      if (key[i] == kHashEmpty) continue;
+      // first slot: the key's low 32 bits scaled to [0, SLOTS)
+      uint32_t h = (uint32_t)(((uint64_t)(uint32_t)key[i] * SM::SLOTS) >> 32);
+      for (;;) {  // at most n < SLOTS probes: the table is never full
+        const unsigned long long old = atomicCAS(&s.tk[h], kHashEmpty, key[i]);
+        if (old == kHashEmpty || old == key[i]) break;
+        h = h + 1 == (uint32_t)SM::SLOTS ? 0u : h + 1;
+      }
+      atomicAdd(&s.tc[h], 1u);
+    }
+    __syncthreads();
+    // occupied slots are the tile's distinct keys
+    uint32_t n_groups = 0, n_keep = 0;
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      const uint32_t c = s.tc[q * THREADS + tid];
+      n_groups += c != 0;
+      n_keep += c >= out.ci && c <= out.cx;
+    }
+    uint64_t tot2;
+    const uint64_t pre = block_excl_scan<uint64_t, THREADS>(((uint64_t)n_groups << 32) | n_keep, s.ws64, &tot2);
+    uint32_t kb = (uint32_t)pre;
+    const uint32_t ktot = (uint32_t)tot2;
+    if (tid == 0) {
+      s.base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
+      atomicAdd(out.n_distinct, tot2 >> 32);
+    }
+    __syncthreads();
+    const uint64_t base = s.base;
+    if (base + ktot > out.cap) {
+      if (tid == 0) atomicOr(err, ERR_CAPACITY);
+    } else if (n_keep) {
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        const uint32_t c = s.tc[q * THREADS + tid];
+        if (c >= out.ci && c <= out.cx) {
+          out.keys[base + kb] = out.mixer.unmix(s.tk[q * THREADS + tid]);
+          out.counts[base + kb] = c;
+          if (out.slots) out.slots[base + kb] = cur.group / out.bins_per_slot;
+          ++kb;
+        }
+      }
+    }
   }
 }
 
