@@ -833,113 +833,87 @@ tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
 
 // ------------------------------------------------------- hashed count tiles
 // Count mode for 64-bit keys below 2^62 (k <= 31): the keys of a tile go
-// into an open-addressing table in shared memory (twice the tile's size,
-// linear probing from the key's low bits, one 64-bit CAS to claim a slot and
-// one atomic add to count), and the occupied slots are the tile's distinct
-// keys.  Same input and output as tile_group_kernel with far fewer steps per
-// key; copies of one key meet at one slot whatever their number.  Tiles are
-// staged by bulk copies into a ring of HASH_STAGES buffers, so that several
-// copies per SM are in flight (one per CTA does not cover HBM latency).
-constexpr int HASH_STAGES = 1;
+// into an open-addressing table in shared memory (1.25 slots per key of a
+// full tile, linear probing from the key's low bits, one 64-bit CAS to claim
+// a slot and one atomic add to count), and the occupied slots are the tile's
+// distinct keys.  Same input and output as tile_group_kernel with far fewer
+// steps per key; copies of one key meet at one slot whatever their number.
+// The tile's keys are read straight into registers (coalesced 8-byte
+// loads): without a staging buffer three CTAs fit an SM and hide the load
+// latency of one another (measured faster than bulk-copy staging, which
+// leaves room for two).
 constexpr int HASH_THREADS = 512;
-constexpr int HASH_SLOTS = 5120;  // 1.25 slots per key of a 4096-key tile
+constexpr int HASH_SLOTS = 5120;
+constexpr unsigned long long kHashEmpty = ~0ull;
 
 template <int THREADS, int IPT>
 struct TileHashSmem {
   static constexpr int TILE = THREADS * IPT;
   static constexpr int SLOTS = HASH_SLOTS;
-  uint64_t a[HASH_STAGES][TILE + 4];  // staged keys (bulk copy targets)
-  unsigned long long tk[SLOTS];       // slot keys (kHashEmpty when free)
-  uint32_t tc[SLOTS];                 // slot counts
+  unsigned long long tk[SLOTS];    // slot keys (kHashEmpty when free)
+  uint32_t tc[SLOTS];              // slot counts
   uint64_t ws64[THREADS / 32 + 1];
-  uint64_t bar[HASH_STAGES];
   unsigned long long base;
-  struct Stage {
-    uint32_t t, n, lead, group;       // t = number of tiles: no tile in this stage
-  } st[HASH_STAGES];
+  unsigned long long start;        // the next tile: first key, index, keys, group
+  uint32_t t, n, group;
 };
-constexpr unsigned long long kHashEmpty = ~0ull;
 
-// Thread 0: claims the next tile that fits (bigger ones go to the big list,
-// empty ones are skipped) and starts its copy into stage b.
-template <int THREADS, int IPT>
-__device__ void hash_issue(const uint64_t *keys, const TilePlan &plan, uint32_t nt, uint32_t *work,
-                           TileHashSmem<THREADS, IPT> &s, int b, uint32_t *big_list, uint32_t *n_big,
-                           unsigned long long *big_keys, uint32_t big_cap, uint32_t *err) {
-  using SM = TileHashSmem<THREADS, IPT>;
+// Thread 0: claims the next tile that fits (bigger ones go to the big list)
+// and records it in s.start/t/n/group (t = number of tiles when none is left).
+template <typename SM>
+__device__ void hash_claim(SM &s, const TilePlan &plan, uint32_t nt, uint32_t *work, uint32_t *big_list,
+                           uint32_t *n_big, unsigned long long *big_keys, uint32_t big_cap, uint32_t *err) {
   for (;;) {
     const uint32_t t = atomicAdd(work, 1u);
-    if (t >= nt) {
-      s.st[b].t = nt;
-      return;
-    }
+    s.t = t;
+    if (t >= nt) return;
     const TileDesc d = plan.desc[t];
     if (d.n == 0) continue;
     if (d.n > (uint32_t)SM::TILE) {
       push_big(t, d.n, big_list, n_big, big_keys, big_cap, err);
       continue;
     }
-    // the 16-byte aligned cover of keys[st, st + n) (16 bytes of slack exist)
-    const uintptr_t src = reinterpret_cast<uintptr_t>(keys + d.st);
-    const uintptr_t src0 = src & ~(uintptr_t)15;
-    const uint32_t bytes = (uint32_t)((src + (uint64_t)d.n * 8 - src0 + 15) & ~(uintptr_t)15);
-    s.st[b] = {t, d.n, (uint32_t)((src - src0) / 8), d.group};
-    fence_proxy_async_smem();
-    bulk_load(s.a[b], reinterpret_cast<const void *>(src0), bytes, &s.bar[b]);
+    s.start = d.st;
+    s.n = d.n;
+    s.group = d.group;
     return;
   }
 }
 
 template <int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS, 2048 / THREADS > 1 ? 2 : 1)
+__global__ void __launch_bounds__(THREADS, 3)
 tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<uint64_t> out,
                  uint32_t *big_list, uint32_t *n_big, unsigned long long *big_keys, uint32_t big_cap,
                  uint32_t *err) {
   using SM = TileHashSmem<THREADS, IPT>;
   constexpr int SPT = SM::SLOTS / THREADS;  // slots per thread
-  static_assert(SM::SLOTS % THREADS == 0 && SM::SLOTS > SM::TILE && offsetof(SM, a) == 0 &&
-                ((SM::TILE + 4) * 8) % 16 == 0, "layout");
+  static_assert(SM::SLOTS % THREADS == 0 && SM::SLOTS > SM::TILE, "layout");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const uint32_t nt = *plan.n_tiles;
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int b = 0; b < HASH_STAGES; ++b) mbar_init(&s.bar[b], 1);
-    for (int b = 0; b < HASH_STAGES; ++b)
-      hash_issue<THREADS, IPT>(keys, plan, nt, work, s, b, big_list, n_big, big_keys, big_cap, err);
-  }
+  if (tid == 0) hash_claim(s, plan, nt, work, big_list, n_big, big_keys, big_cap, err);
   __syncthreads();
-  uint32_t parity = 0;  // bit b: phase parity of stage b's barrier
-  for (int b = 0;; b = (b + 1 == HASH_STAGES) ? 0 : b + 1) {
-    const typename SM::Stage cur = s.st[b];
-    if (cur.t >= nt) break;  // stages are filled in order: nothing after this either
-    const int n = (int)cur.n, lead = (int)cur.lead;
-    // thread 0 waits for the copy; the barrier passes its result (and the
-    // copied data) on to the others, and ends the previous tile
-    const bool ok = tid != 0 || mbar_wait(&s.bar[b], (parity >> b) & 1u);
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) {
-        atomicOr(err, ERR_TIMEOUT);
-        for (int q = 0; q < HASH_STAGES; ++q)
-          if (s.st[q].t < nt) mbar_wait(&s.bar[q], (parity >> q) & 1u);
-      }
-      return;
-    }
-    parity ^= 1u << b;
-    // clear the table (thread t owns slots t, t + THREADS, ...) and take the tile's keys
+  for (;;) {
+    if (s.t >= nt) break;
+    const int n = (int)s.n;
+    const uint64_t *src = keys + s.start;
+    const uint32_t group = s.group;
+    // clear the table (thread t owns slots t, t + THREADS, ...)
 #pragma unroll
     for (int q = 0; q < SPT; ++q) {
       s.tk[q * THREADS + tid] = kHashEmpty;
       s.tc[q * THREADS + tid] = 0;
     }
+    __syncthreads();  // table clear; the tile's record has been read by all
+    // the next tile is claimed while this one is counted
+    if (tid == 0) hash_claim(s, plan, nt, work, big_list, n_big, big_keys, big_cap, err);
     uint64_t key[IPT];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const int e = tid + i * THREADS;
-      key[i] = e < n ? s.a[b][lead + e] : kHashEmpty;
+      key[i] = e < n ? src[e] : kHashEmpty;
     }
-    __syncthreads();  // stage b consumed, table clear
-    if (tid == 0) hash_issue<THREADS, IPT>(keys, plan, nt, work, s, b, big_list, n_big, big_keys, big_cap, err);
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       if (key[i] == kHashEmpty) continue;
@@ -980,11 +954,12 @@ tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *wor
         if (c >= out.ci && c <= out.cx) {
           out.keys[base + kb] = out.mixer.unmix(s.tk[q * THREADS + tid]);
           out.counts[base + kb] = c;
-          if (out.slots) out.slots[base + kb] = cur.group / out.bins_per_slot;
+          if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
           ++kb;
         }
       }
     }
+    __syncthreads();  // the table is read above before the next tile clears it
   }
 }
 

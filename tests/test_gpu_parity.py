@@ -71,6 +71,18 @@ def test_mid_workload_scaled(k):
     assert_same(got, oracle_count(w.bases, w.offsets, k))
 
 
+@pytest.mark.parametrize("k,ci", [(31, 1), (25, 1), (32, 1), (28, 2)])
+def test_mostly_distinct_keys_fill_the_tiles(k, ci):
+    # iid random reads: nearly every k-mer is distinct, so the hashed tiles
+    # run close to their load limit (and k=32 takes the grouping kernel)
+    rng = np.random.default_rng(77)
+    n_reads, L = 120_000, 150
+    bases = np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, n_reads * L)]
+    offsets = np.arange(0, (n_reads + 1) * L, L, dtype=np.uint64)
+    got = gpu_count(bases, offsets, k, m=7, n_bins=16, cutoff_min=ci)
+    assert_same(got, oracle_count(bases, offsets, k, ci))
+
+
 def test_one_bin_takes_the_wide_digit_path():
     # ~19 M k-mers in one bin need 14 digit bits, more than a unit
     # histogram holds: the partition then reserves places per warp and digit
