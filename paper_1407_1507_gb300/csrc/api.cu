@@ -198,6 +198,12 @@ void release_all(Handle &h) {
     if (h.ds.buf_free[i]) cudaEventDestroy(h.ds.buf_free[i]);
     h.ds.copy_done[i] = h.ds.buf_free[i] = nullptr;
   }
+  if (h.ss.meta_done) cudaEventSynchronize(h.ss.meta_done);
+  if (h.ss.meta_host) cudaFreeHost(h.ss.meta_host);
+  h.ss.meta_host = nullptr;
+  h.ss.meta_host_cap = 0;
+  if (h.ss.meta_done) cudaEventDestroy(h.ss.meta_done);
+  h.ss.meta_done = nullptr;
   if (h.ds.go) cudaEventDestroy(h.ds.go);
   h.ds.go = nullptr;
   if (h.ds.copy_st) {

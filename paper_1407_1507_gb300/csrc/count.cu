@@ -308,15 +308,30 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   if (dev_ensure(ss.counters, 64, h.st) || dev_ensure(ss.cursor, meta_bytes, h.st) ||
       dev_ensure(ss.hist, NB * 4 + 4, h.st))
     return KMC_ENOMEM;
-  std::vector<uint8_t> meta(o_bf);  // the fill counters are zeroed on the device
-  memcpy(meta.data(), chunks.data(), chunks.size() * sizeof(Chunk));
-  memcpy(meta.data() + o_pd, pds.data(), pds.size() * sizeof(PieceDesc));
-  memcpy(meta.data() + o_gb, gbase.data(), (B + 1) * 4);
-  memcpy(meta.data() + o_gd, gD.data(), B);
-  if (!units.empty()) memcpy(meta.data() + o_un, units.data(), units.size() * sizeof(PartUnit));
-  memcpy(meta.data() + o_kb, kbase.data(), (B + 1) * 8);
-  memcpy(meta.data() + o_sg, sbase.data(), (B + 1) * 4);
-  KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta.data(), o_bf, cudaMemcpyHostToDevice, h.st));
+  // staged in a pinned buffer (the fill counters are zeroed on the device);
+  // the previous upload from it has finished before it is rewritten
+  if (ss.meta_done) KMC_CUDA_TRY(cudaEventSynchronize(ss.meta_done));
+  if (ss.meta_host_cap < o_bf) {
+    if (ss.meta_host) cudaFreeHost(ss.meta_host);
+    ss.meta_host = nullptr;
+    ss.meta_host_cap = 0;
+    if (cudaHostAlloc(&ss.meta_host, o_bf + (o_bf >> 2), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return KMC_ENOMEM;
+    }
+    ss.meta_host_cap = o_bf + (o_bf >> 2);
+  }
+  if (!ss.meta_done) KMC_CUDA_TRY(cudaEventCreateWithFlags(&ss.meta_done, cudaEventDisableTiming));
+  uint8_t *meta = static_cast<uint8_t *>(ss.meta_host);
+  memcpy(meta, chunks.data(), chunks.size() * sizeof(Chunk));
+  memcpy(meta + o_pd, pds.data(), pds.size() * sizeof(PieceDesc));
+  memcpy(meta + o_gb, gbase.data(), (B + 1) * 4);
+  memcpy(meta + o_gd, gD.data(), B);
+  if (!units.empty()) memcpy(meta + o_un, units.data(), units.size() * sizeof(PartUnit));
+  memcpy(meta + o_kb, kbase.data(), (B + 1) * 8);
+  memcpy(meta + o_sg, sbase.data(), (B + 1) * 4);
+  KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta, o_bf, cudaMemcpyHostToDevice, h.st));
+  KMC_CUDA_TRY(cudaEventRecord(ss.meta_done, h.st));
   char *base = static_cast<char *>(ss.cursor.p);
   m->n_chunks = chunks.size();
   m->NB = NB;

@@ -75,6 +75,10 @@ struct SortScratch {
   // second level of the (k,x)-mer path: expanded, weighted k-mers
   DevBuf l2_hist, l2_base, l2_flags, l2_fscan, l2_tfirst, l2_tmp, l2_keys, l2_wts, l2_big,
       l2_big_k, l2_big_v, l2_grp, l2_counters, l2_out_keys, l2_out_counts;
+  // pinned staging of the sort metadata (chunks, units, bin tables)
+  void *meta_host = nullptr;
+  size_t meta_host_cap = 0;
+  cudaEvent_t meta_done = nullptr;
   // what kmc_debug_bin_keys needs to find and decode one bin's keys
   std::vector<uint32_t> dbg_group_base;
   int dbg_key_bytes = 0;

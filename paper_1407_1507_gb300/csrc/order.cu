@@ -13,7 +13,7 @@ namespace kmc {
 namespace {
 
 constexpr int PAIR_THREADS = 256;
-constexpr int PAIR_IPT = 16;  // tile = 4096 pairs
+constexpr int PAIR_IPT = 8;   // tile = 2048 pairs (three CTAs per SM)
 constexpr int PAIR_BIG_IPT = 8;
 constexpr int PAIR_MAX_D = 22;
 

@@ -973,7 +973,7 @@ struct TilePairsSmem {
 };
 
 template <typename K, typename V, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 3)
 tile_pairs_kernel(K *keys, V *vals, TilePlan plan, uint32_t *work, uint32_t *big_list,
                   uint32_t *n_big, unsigned long long *big_keys, uint32_t big_cap,
                   uint32_t *err) {
