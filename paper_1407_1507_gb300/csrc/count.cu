@@ -246,6 +246,40 @@ struct SortMeta {
 
 // unit_keys > 0 asks for the generate + sweep path (x = 0, units of
 // unit_keys keys); it is taken when the bins' k-mers add up.
+// Largest i in [0, n) with first[i] <= x (first[0] <= x < first[n]).
+__device__ __forceinline__ uint32_t meta_find(const uint32_t *first, uint32_t n, uint32_t x) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (first[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Chunk c of the (piece, bin) pair i with cpos[i] <= c < cpos[i+1]: records
+// from rec_base[p][b] + (c - cpos[i]) * KX_RECORDS_PER_CHUNK on.
+__global__ void meta_chunks_kernel(const uint64_t *const *rec_base, const uint32_t *cpos, uint32_t P,
+                                   uint32_t B, uint32_t n_chunks, Chunk *chunks) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_chunks; c += gridDim.x * blockDim.x) {
+    const uint32_t i = meta_find(cpos, P * B, c);
+    const uint32_t p = i / B, b = i % B;
+    const uint64_t r = rec_base[p][b] + (uint64_t)(c - cpos[i]) * KX_RECORDS_PER_CHUNK;
+    const uint64_t r1 = rec_base[p][b + 1];
+    chunks[c] = Chunk{r, (uint32_t)(r1 - r < KX_RECORDS_PER_CHUNK ? r1 - r : KX_RECORDS_PER_CHUNK), p, b, 0u};
+  }
+}
+
+// Unit u of bin b with ubase[b] <= u < ubase[b+1]: keys from
+// kbase[b] + (u - ubase[b]) * unit_keys on.
+__global__ void meta_units_kernel(const uint64_t *kbase, const uint32_t *ubase, uint32_t B,
+                                  uint32_t unit_keys, uint32_t n_units, PartUnit *units) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
+    const uint32_t b = meta_find(ubase, B, u);
+    const uint64_t o = kbase[b] + (uint64_t)(u - ubase[b]) * unit_keys, k1 = kbase[b + 1];
+    units[u] = PartUnit{o, (uint32_t)(k1 - o < unit_keys ? k1 - o : unit_keys), b};
+  }
+}
+
 // Only the bins of the wave [wb0, wb1) take part (the others are empty).
 int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta *m,
                uint32_t unit_keys = 0, uint32_t wb0 = 0, uint32_t wb1 = ~0u) {
@@ -267,40 +301,50 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   }
   gbase[B] = (uint32_t)NB;
   if (NB >= 0xFFFFFFF0ull) return KMC_EINVAL;
+  // per bin: first key, first super bucket, first unit; per (piece, bin):
+  // first chunk.  The chunks and units themselves are written on the device.
   std::vector<uint64_t> kbase(B + 1, 0);
-  std::vector<uint32_t> sbase(B + 1, 0);
-  std::vector<PartUnit> units;
+  std::vector<uint32_t> sbase(B + 1, 0), ubase(B + 1, 0);
   bool gen = unit_keys > 0;
   if (gen) {
     for (uint32_t b = 0; b < B; ++b) {
       kbase[b + 1] = kbase[b] + bk[b];
       sbase[b + 1] = sbase[b] + (1u << std::min<int>(gD[b], SWEEP_UPPER));
-      for (uint64_t o = 0; o < bk[b]; o += unit_keys)
-        units.push_back({kbase[b] + o, (uint32_t)std::min<uint64_t>(unit_keys, bk[b] - o), b});
+      ubase[b + 1] = ubase[b] + (uint32_t)((bk[b] + unit_keys - 1) / unit_keys);
     }
     if (wb0 == 0 && wb1 == B && kbase[B] != h.stats.n_kmer_positions) gen = false;
-    if (!gen) units.clear();
   }
+  const uint32_t n_units = gen ? ubase[B] : 0;
   const uint32_t n_super = gen ? sbase[B] : 0;
-  std::vector<Chunk> chunks;
+  const size_t P = h.pieces.size();
   std::vector<PieceDesc> pds;
-  for (size_t p = 0; p < h.pieces.size(); ++p) {
+  std::vector<const uint64_t *> rbp;
+  std::vector<uint32_t> cpos(P * B + 1, 0);
+  for (size_t p = 0; p < P; ++p) {
     Piece *pc = h.pieces[p];
     pds.push_back({pc->d_index, pc->d_words});
+    rbp.push_back(static_cast<const uint64_t *>(pc->rec_base.p));
     const std::vector<uint64_t> &rb = pc->rec_base_host;
-    for (uint32_t b = wb0; b < wb1; ++b)
-      for (uint64_t r = rb[b]; r < rb[b + 1]; r += KX_RECORDS_PER_CHUNK)
-        chunks.push_back({r, (uint32_t)std::min<uint64_t>(KX_RECORDS_PER_CHUNK, rb[b + 1] - r),
-                          (uint32_t)p, b, 0});
+    for (uint32_t b = 0; b < B; ++b) {
+      const uint64_t nr = (b >= wb0 && b < wb1) ? rb[b + 1] - rb[b] : 0;
+      cpos[p * B + b + 1] = cpos[p * B + b] + (uint32_t)((nr + KX_RECORDS_PER_CHUNK - 1) / KX_RECORDS_PER_CHUNK);
+    }
   }
+  const uint32_t n_chunks = cpos[P * B];
   auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  const size_t o_pd = up16((chunks.size() + 1) * sizeof(Chunk));
-  const size_t o_gb = o_pd + up16((pds.size() + 1) * sizeof(PieceDesc));
+  // uploaded part
+  const size_t o_pd = 0;
+  const size_t o_gb = o_pd + up16((P + 1) * sizeof(PieceDesc));
   const size_t o_gd = o_gb + up16((B + 1) * 4);
-  const size_t o_un = o_gd + up16(B + 1);
-  const size_t o_kb = o_un + up16((units.size() + 1) * sizeof(PartUnit));
+  const size_t o_kb = o_gd + up16(B + 1);
   const size_t o_sg = o_kb + up16((B + 1) * 8);
-  const size_t o_bf = o_sg + up16((B + 1) * 4);  // device-only from here on
+  const size_t o_ub = o_sg + up16((B + 1) * 4);
+  const size_t o_cp = o_ub + up16((B + 1) * 4);
+  const size_t o_rb = o_cp + up16((P * B + 1) * 4);
+  const size_t o_up = o_rb + up16((P + 1) * 8);  // device-only from here on
+  const size_t o_ch = o_up;
+  const size_t o_un = o_ch + up16(((size_t)n_chunks + 1) * sizeof(Chunk));
+  const size_t o_bf = o_un + up16(((size_t)n_units + 1) * sizeof(PartUnit));
   const size_t o_sh = o_bf + up16((B + 1) * 8);
   const size_t o_sc = o_sh + up16((n_super + 1) * 4);
   const size_t o_sb = o_sc + up16((n_super + 1) * 8);
@@ -308,39 +352,40 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   if (dev_ensure(ss.counters, 64, h.st) || dev_ensure(ss.cursor, meta_bytes, h.st) ||
       dev_ensure(ss.hist, NB * 4 + 4, h.st))
     return KMC_ENOMEM;
-  // staged in a pinned buffer (the fill counters are zeroed on the device);
-  // the previous upload from it has finished before it is rewritten
+  // staged in a pinned buffer; the previous upload from it has finished
+  // before it is rewritten
   if (ss.meta_done) KMC_CUDA_TRY(cudaEventSynchronize(ss.meta_done));
-  if (ss.meta_host_cap < o_bf) {
+  if (ss.meta_host_cap < o_up) {
     if (ss.meta_host) cudaFreeHost(ss.meta_host);
     ss.meta_host = nullptr;
     ss.meta_host_cap = 0;
-    if (cudaHostAlloc(&ss.meta_host, o_bf + (o_bf >> 2), cudaHostAllocDefault) != cudaSuccess) {
+    if (cudaHostAlloc(&ss.meta_host, o_up + (o_up >> 2), cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       return KMC_ENOMEM;
     }
-    ss.meta_host_cap = o_bf + (o_bf >> 2);
+    ss.meta_host_cap = o_up + (o_up >> 2);
   }
   if (!ss.meta_done) KMC_CUDA_TRY(cudaEventCreateWithFlags(&ss.meta_done, cudaEventDisableTiming));
   uint8_t *meta = static_cast<uint8_t *>(ss.meta_host);
-  memcpy(meta, chunks.data(), chunks.size() * sizeof(Chunk));
-  memcpy(meta + o_pd, pds.data(), pds.size() * sizeof(PieceDesc));
+  memcpy(meta + o_pd, pds.data(), P * sizeof(PieceDesc));
   memcpy(meta + o_gb, gbase.data(), (B + 1) * 4);
   memcpy(meta + o_gd, gD.data(), B);
-  if (!units.empty()) memcpy(meta + o_un, units.data(), units.size() * sizeof(PartUnit));
   memcpy(meta + o_kb, kbase.data(), (B + 1) * 8);
   memcpy(meta + o_sg, sbase.data(), (B + 1) * 4);
-  KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta, o_bf, cudaMemcpyHostToDevice, h.st));
+  memcpy(meta + o_ub, ubase.data(), (B + 1) * 4);
+  memcpy(meta + o_cp, cpos.data(), (P * B + 1) * 4);
+  memcpy(meta + o_rb, rbp.data(), P * 8);
+  KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta, o_up, cudaMemcpyHostToDevice, h.st));
   KMC_CUDA_TRY(cudaEventRecord(ss.meta_done, h.st));
   char *base = static_cast<char *>(ss.cursor.p);
-  m->n_chunks = chunks.size();
+  m->n_chunks = n_chunks;
   m->NB = NB;
-  m->chunks = reinterpret_cast<const Chunk *>(base);
+  m->chunks = reinterpret_cast<const Chunk *>(base + o_ch);
   m->pieces = reinterpret_cast<const PieceDesc *>(base + o_pd);
   m->group_base = reinterpret_cast<const uint32_t *>(base + o_gb);
   m->group_D = reinterpret_cast<const uint8_t *>(base + o_gd);
   m->gen = gen;
-  m->n_units = units.size();
+  m->n_units = n_units;
   m->units = reinterpret_cast<const PartUnit *>(base + o_un);
   m->bin_key_base = reinterpret_cast<const uint64_t *>(base + o_kb);
   m->sgroup_base = reinterpret_cast<const uint32_t *>(base + o_sg);
@@ -349,6 +394,19 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   m->super_hist = reinterpret_cast<uint32_t *>(base + o_sh);
   m->super_cursor = reinterpret_cast<unsigned long long *>(base + o_sc);
   m->super_base = reinterpret_cast<unsigned long long *>(base + o_sb);
+  if (n_chunks) {
+    meta_chunks_kernel<<<std::min<uint32_t>((n_chunks + 255) / 256, 4096), 256, 0, h.st>>>(
+        reinterpret_cast<const uint64_t *const *>(base + o_rb), reinterpret_cast<const uint32_t *>(base + o_cp),
+        (uint32_t)P, B, n_chunks, reinterpret_cast<Chunk *>(base + o_ch));
+    KMC_COUNT_LAUNCH();
+  }
+  if (n_units) {
+    meta_units_kernel<<<std::min<uint32_t>((n_units + 255) / 256, 4096), 256, 0, h.st>>>(
+        reinterpret_cast<const uint64_t *>(base + o_kb), reinterpret_cast<const uint32_t *>(base + o_ub), B,
+        unit_keys, n_units, reinterpret_cast<PartUnit *>(base + o_un));
+    KMC_COUNT_LAUNCH();
+  }
+  KMC_CUDA_TRY(cudaGetLastError());
   if (gen)  // fill counters, super histogram and cursors start at zero
     KMC_CUDA_TRY(cudaMemsetAsync(base + o_bf, 0, o_sb - o_bf, h.st));
   ss.dbg_group_base = gbase;
