@@ -72,8 +72,9 @@ typedef struct {
   uint32_t debug_flags;/* KMC_DEBUG_* bits: keep intermediates for inspection     */
   uint32_t reserved0;  /* must be zero                                            */
   uint64_t piece_bytes;/* reads are distributed in pieces of about this many
-                          bytes (0 = 1 GiB); bounds the distribution scratch,
-                          never changes the result                            */
+                          bytes (0 = 256 MiB: a piece's bins then stay close
+                          to L2-sized while they are filled); bounds the
+                          distribution scratch, never changes the result      */
   uint64_t device_budget; /* device bytes for the bins and the sort buffers
                           (0 = no limit).  With a limit, a piece whose bins
                           would take the bins past half of it is moved to

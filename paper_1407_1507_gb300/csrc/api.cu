@@ -16,7 +16,7 @@
 namespace kmc {
 
 namespace {
-constexpr uint64_t kDefaultPieceBytes = 1ull << 30;  // distribution works on pieces of ~1 GiB
+constexpr uint64_t kDefaultPieceBytes = 1ull << 28;  // distribution works on pieces of ~256 MiB
 constexpr uint64_t kSampleReads = 1ull << 20;   // bin-map sample (Sect. 2.4)
 constexpr uint64_t kSampleBytes = 1ull << 28;
 
