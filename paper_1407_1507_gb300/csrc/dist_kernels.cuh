@@ -70,26 +70,33 @@ pack_kernel(const uint8_t *__restrict__ aligned, uint64_t n_stream, uint32_t mis
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const uint64_t cq = q0 + 16 * c;
-      uint8_t by[16];
+      uint32_t wd[4];
       if (cq >= mis && cq + 16 <= n_stream) {
-        uint4 v = *reinterpret_cast<const uint4 *>(aligned + cq);
-        memcpy(by, &v, 16);
-      } else {
+        const uint4 v = *reinterpret_cast<const uint4 *>(aligned + cq);
+        wd[0] = v.x; wd[1] = v.y; wd[2] = v.z; wd[3] = v.w;
+      } else {  // a stream edge: bytes outside [mis, n_stream) read as 'N'
+        uint8_t by[16];
         for (int j = 0; j < 16; ++j) {
-          uint64_t q = cq + j;
+          const uint64_t q = cq + j;
           by[j] = (q >= mis && q < n_stream) ? aligned[q] : (uint8_t)'N';
         }
+        memcpy(wd, by, 16);
       }
+      // four bases per 32-bit word (byte j = base j): codes from bits 1-2
+      // and 2-3 of each byte; a byte is a base when it equals "ACGT"[code]
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = 16 * c + j;  // 0..63
-        bool ok;
-        unsigned code = base_code(by[j], &ok);
-        const uint64_t q = q0 + i;
-        if (q < mis || q >= n_stream) ok = false;
-        if (!ok) code = 0;
-        pw[i >> 5] |= (uint64_t)code << (62 - 2 * (i & 31));
-        if (!ok) iv |= 1ull << (63 - i);
+      for (int qw = 0; qw < 4; ++qw) {
+        const uint32_t w = wd[qw];
+        uint32_t cd = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
+        const uint32_t sel = (cd & 0x3u) | ((cd >> 4) & 0x30u) | ((cd >> 8) & 0x300u) | ((cd >> 12) & 0x3000u);
+        const uint32_t ok = __vcmpeq4(w, __byte_perm(0x54474341u, 0u, sel));  // 0xFF per base
+        cd &= ok;
+        const uint32_t g8 = ((cd & 3u) << 6) | (((cd >> 8) & 3u) << 4) | (((cd >> 16) & 3u) << 2) | (cd >> 24);
+        const uint32_t nb = ~ok;
+        const uint32_t i4 = ((nb >> 4) & 8u) | ((nb >> 13) & 4u) | ((nb >> 22) & 2u) | (nb >> 31);
+        const int kq = 4 * c + qw;  // bases 4 kq .. 4 kq + 3 of the thread's 64
+        pw[kq >> 3] |= (uint64_t)g8 << (56 - 8 * (kq & 7));
+        iv |= (uint64_t)i4 << (60 - 4 * kq);
       }
     }
   }
