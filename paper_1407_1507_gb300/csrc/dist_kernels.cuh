@@ -396,13 +396,19 @@ __host__ __device__ inline int sig2_stride(int k, int m) {
 __host__ __device__ inline int sig2_hist_bins(uint32_t n_bins) {
   return n_bins <= (uint32_t)SIG_SMEM_BINS ? (int)n_bins : 0;
 }
+// m-mer values and signatures are kept as 16-bit words when m <= 7 (the
+// sentinel 4^m fits), which halves the largest shared array and lets more
+// CTAs share an SM.
+inline size_t sig2_value_bytes(int m) { return m <= 7 ? 2 : 4; }
 inline size_t sig2_smem_bytes(int k, int m, uint32_t n_bins) {
+  const size_t vb = 2 * (size_t)SIG2_LANES * sig2_stride(k, m) * sig2_value_bytes(m);
   return (size_t)SIG2_PWORDS * 8 + 4 * (size_t)SIG2_MWORDS * 8 + (size_t)SIG2_LANES * 8 +
-         2 * (size_t)SIG2_LANES * sig2_stride(k, m) * 4 + (size_t)sig2_hist_bins(n_bins) * 8;
+         ((vb + 7) & ~(size_t)7) + (size_t)sig2_hist_bins(n_bins) * 8;
 }
 // The lane-block form pays off once a block holds several positions.
 inline bool sig2_applies(int k, int m) { return k - m + 1 >= 8 && k - m + 1 <= SIG2_MAXW; }
 
+template <typename VT>
 __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = threadIdx.x;
@@ -421,10 +427,11 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   uint64_t *cm = sm + SIG2_MWORDS;                      // invalid base or read start
   int64_t *lastw = reinterpret_cast<int64_t *>(cm + SIG2_MWORDS);
   int64_t *fbrk = lastw + SIG2_MWORDS;                  // first break of each lane's block
-  uint32_t *V = reinterpret_cast<uint32_t *>(fbrk + SIG2_LANES);   // values, then signatures
-  uint32_t *P = V + SIG2_LANES * stride;                           // prefix minima
+  VT *V = reinterpret_cast<VT *>(fbrk + SIG2_LANES);   // values, then signatures
+  VT *P = V + SIG2_LANES * stride;                     // prefix minima
   // per-bin records | words << 21 | k-mers << 42 of this CTA (fields < 2^21)
-  unsigned long long *hpk = reinterpret_cast<unsigned long long *>(P + SIG2_LANES * stride);
+  unsigned long long *hpk = reinterpret_cast<unsigned long long *>(
+      (reinterpret_cast<uintptr_t>(P + SIG2_LANES * stride) + 7) & ~(uintptr_t)7);
   __shared__ uint32_t ws[SIG2_LANES / 32 + 1];
   __shared__ int64_t rs0;
   __shared__ unsigned long long out_base;
@@ -514,9 +521,9 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
       rc = (rc >> 2) | ((3u - c) << rsh);
       const uint32_t cn = fw < rc ? fw : rc;                 // canonical m-mer (Sect. 2.1)
       const uint32_t v = mmer_allowed(cn, m) ? cn : SENT;     // Sect. 2.2 filter
-      V[L * stride + j] = v;
+      V[L * stride + j] = (VT)v;
       pm = v < pm ? v : pm;
-      P[L * stride + j] = pm;
+      P[L * stride + j] = (VT)pm;
     }
   }
   __syncthreads();
@@ -526,8 +533,8 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
     for (int j = w - 1; j >= 0; --j) {
       const uint32_t v = V[L * stride + j];
       sfx = v < sfx ? v : sfx;
-      const uint32_t nx = j > 0 ? P[(L + 1) * stride + j - 1] : 0xFFFFFFFFu;
-      V[L * stride + j] = sfx < nx ? sfx : nx;
+      const uint32_t nx = j > 0 ? (uint32_t)P[(L + 1) * stride + j - 1] : 0xFFFFFFFFu;
+      V[L * stride + j] = (VT)(sfx < nx ? sfx : nx);
     }
   }
   __syncthreads();
@@ -681,7 +688,10 @@ inline cudaError_t sig_prepare() {
   if (dev < 64 && done[dev].load()) return cudaSuccess;
   e = cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SigSmem));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sig2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(sig2_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sig2_smem_bytes(SIG2_MAXW, 8, SIG_SMEM_BINS));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(sig2_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sig2_smem_bytes(SIG2_MAXW, 1, SIG_SMEM_BINS));
   if (e != cudaSuccess) return e;
   if (dev < 64) done[dev].store(1);
@@ -696,7 +706,10 @@ inline int sig_launch(const SigArgs &a, uint64_t n_stream, bool tile, cudaStream
     const uint64_t own = (uint64_t)sig2_own(a.k, a.m);
     const uint64_t g = (n_stream + own - 1) / own;
     if (g == 0) return 0;
-    sig2_kernel<<<(unsigned)g, SIG2_LANES, sig2_smem_bytes(a.k, a.m, a.n_bins), st>>>(a);
+    if (a.m <= 7)
+      sig2_kernel<uint16_t><<<(unsigned)g, SIG2_LANES, sig2_smem_bytes(a.k, a.m, a.n_bins), st>>>(a);
+    else
+      sig2_kernel<uint32_t><<<(unsigned)g, SIG2_LANES, sig2_smem_bytes(a.k, a.m, a.n_bins), st>>>(a);
     return 1;
   }
   const uint64_t g = (n_stream + SIG_TPOS - 1) / SIG_TPOS;
@@ -814,6 +827,45 @@ __global__ void map_assign_kernel(const uint64_t *keys, const uint64_t *prefix, 
     const uint64_t wt = 0xFFFFFFFFull - (keys[i] >> 24);
     map[sg] = (wt == 0 || total == 0) ? sg % n_bins : (uint32_t)((prefix[i] * n_bins) / total);
   }
+}
+
+// The same map without a sort, for up to MAP_DIRECT_MAX signatures: the
+// weight preceding signature s in the order above is summed directly,
+// W(s) = sum of w(t) over the t with w(t) > w(s), or w(t) = w(s) and t < s
+// (weights clamped to 32 bits as in the sort key).  CTA (x, y) takes
+// signatures [256x, 256x + 256) against the y-th slice of all signatures.
+constexpr uint32_t MAP_DIRECT_MAX = 16384;
+constexpr int MAP_DIRECT_SLICES = 16;
+__global__ void __launch_bounds__(256) map_prefix_kernel(const unsigned long long *__restrict__ w, uint32_t n_sig,
+                                                         unsigned long long *__restrict__ before,
+                                                         unsigned long long *__restrict__ total) {
+  __shared__ uint32_t ws[1024];
+  const uint32_t sg = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t my = sg < n_sig ? (uint32_t)min(w[sg], 0xFFFFFFFFull) : 0u;
+  const uint32_t per = (n_sig + gridDim.y - 1) / gridDim.y;
+  const uint32_t t0 = blockIdx.y * per, t1 = min(t0 + per, n_sig);
+  unsigned long long acc = 0;
+  for (uint32_t c = t0; c < t1; c += 1024) {
+    const uint32_t m = min(1024u, t1 - c);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ws[i] = (uint32_t)min(w[c + i], 0xFFFFFFFFull);
+    __syncthreads();
+    for (uint32_t j = 0; j < m; ++j) {
+      const uint32_t x = ws[j];
+      if (x > my || (x == my && c + j < sg)) acc += x;
+    }
+  }
+  if (sg < n_sig && my) {
+    if (acc) atomicAdd(&before[sg], acc);
+    if (blockIdx.y == 0) atomicAdd(total, (unsigned long long)my);
+  }
+}
+__global__ void map_direct_assign_kernel(const unsigned long long *w, const unsigned long long *before,
+                                         const unsigned long long *total, uint32_t n_sig, uint32_t n_bins,
+                                         uint32_t *map) {
+  const uint64_t tot = *total;
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sig; s += gridDim.x * blockDim.x)
+    map[s] = (w[s] == 0 || tot == 0) ? s % n_bins : (uint32_t)((before[s] * n_bins) / tot);
 }
 
 // Converts the raw super k-mer list of a piece into (read index, position in

@@ -123,6 +123,20 @@ int build_bin_map(Handle &h, const char *piece_ptr, const uint64_t *d_offsets, u
   rc = launch_sig(h, a, si.n_stream, KMC_STAGE_BIN_MAP);
   if (rc) return rc;
   StageScope sc(h, KMC_STAGE_BIN_MAP);
+  if (n_sig <= MAP_DIRECT_MAX) {
+    // keys/keys2 hold the preceding weights and the total
+    auto *before = reinterpret_cast<unsigned long long *>(keys);
+    auto *total = reinterpret_cast<unsigned long long *>(keys2);
+    KMC_CUDA_TRY(cudaMemsetAsync(before, 0, (size_t)n_sig * 8 + 8, h.st));
+    map_prefix_kernel<<<dim3((n_sig + 255) / 256, MAP_DIRECT_SLICES), 256, 0, h.st>>>(wt, n_sig, before, total);
+    KMC_COUNT_LAUNCH();
+    map_direct_assign_kernel<<<grid_for(n_sig, 256, 4096), 256, 0, h.st>>>(wt, before, total, n_sig, h.p.n_bins,
+                                                                          as<uint32_t>(h.map));
+    KMC_COUNT_LAUNCH();
+    KMC_CUDA_TRY(cudaGetLastError());
+    h.map_ready = true;
+    return KMC_OK;
+  }
   map_keys_kernel<<<grid_for(n_sig, 256, 4096), 256, 0, h.st>>>(wt, n_sig, keys, vals); KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
   rc = sort_pairs_u64(h, keys, vals, n_sig, 56);
