@@ -374,14 +374,17 @@ __global__ void __launch_bounds__(SIG_THREADS) sig_kernel(SigArgs a) {
 // shared-memory row; the minimum over the window [p, p+w-1] is then the
 // smaller of the suffix minimum of p's block (from p) and the prefix minimum
 // of the next block (to p+w-1): van Herk / Gil-Werman with block size w.
-// Lane 255 only lends its prefix minima, so a CTA covers 255*w positions,
+// The last lane only lends its prefix minima, so a CTA covers 127*w positions,
 // starting one position before the k-mer starts it owns and extending
 // kSuperkmerCap past them (a super k-mer never spans more).
 
 constexpr int SIG2_LANES = 128;
 constexpr int SIG2_MAXW = 64;
-constexpr int SIG2_MWORDS = (SIG2_LANES * SIG2_MAXW + 256) / 64 + 4;  // mask words staged
-constexpr int SIG2_PWORDS = 2 * SIG2_MWORDS;                            // packed words staged
+// Mask words staged per CTA (the lanes' blocks, the k-1 positions after
+// them, alignment); twice as many packed words (32 bases each) are staged.
+__host__ __device__ inline int sig2_mwords(int k, int m) {
+  return (SIG2_LANES * (k - m + 1) + 2 * k + 256) / 64 + 4;
+}
 static_assert((kSuperkmerCap & (kSuperkmerCap - 1)) == 0, "cut test uses a mask");
 // a CTA's per-bin counters are packed in 21-bit fields
 static_assert((SIG2_LANES - 1) * SIG2_MAXW * 8 < (1 << 21), "per-CTA counts fit 21 bits");
@@ -402,7 +405,8 @@ __host__ __device__ inline int sig2_hist_bins(uint32_t n_bins) {
 inline size_t sig2_value_bytes(int m) { return m <= 7 ? 2 : 4; }
 inline size_t sig2_smem_bytes(int k, int m, uint32_t n_bins) {
   const size_t vb = 2 * (size_t)SIG2_LANES * sig2_stride(k, m) * sig2_value_bytes(m);
-  return (size_t)SIG2_PWORDS * 8 + 4 * (size_t)SIG2_MWORDS * 8 + (size_t)SIG2_LANES * 8 +
+  const size_t mw = (size_t)sig2_mwords(k, m);
+  return 2 * mw * 8 + 4 * mw * 8 + (size_t)SIG2_LANES * 8 +
          ((vb + 7) & ~(size_t)7) + (size_t)sig2_hist_bins(n_bins) * 8;
 }
 // The lane-block form pays off once a block holds several positions.
@@ -422,11 +426,12 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   const bool small_bins = hb > 0;
   // shared memory carve-up
   uint64_t *pk = reinterpret_cast<uint64_t *>(smem_raw);
-  uint64_t *iv = pk + SIG2_PWORDS;                      // invalid bases
-  uint64_t *sm = iv + SIG2_MWORDS;                      // read starts
-  uint64_t *cm = sm + SIG2_MWORDS;                      // invalid base or read start
-  int64_t *lastw = reinterpret_cast<int64_t *>(cm + SIG2_MWORDS);
-  int64_t *fbrk = lastw + SIG2_MWORDS;                  // first break of each lane's block
+  const int MW = sig2_mwords(k, m), PW = 2 * MW;
+  uint64_t *iv = pk + PW;                               // invalid bases
+  uint64_t *sm = iv + MW;                               // read starts
+  uint64_t *cm = sm + MW;                               // invalid base or read start
+  int64_t *lastw = reinterpret_cast<int64_t *>(cm + MW);
+  int64_t *fbrk = lastw + MW;                           // first break of each lane's block
   VT *V = reinterpret_cast<VT *>(fbrk + SIG2_LANES);   // values, then signatures
   VT *P = V + SIG2_LANES * stride;                     // prefix minima
   // per-bin records | words << 21 | k-mers << 42 of this CTA (fields < 2^21)
@@ -440,11 +445,11 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   const int64_t LB = pw0 * 32;
   const int64_t mw0 = B0 >= 0 ? B0 / 64 : -1;
   const int64_t LBm = mw0 * 64;
-  for (int i = L; i < SIG2_PWORDS; i += SIG2_LANES) {
+  for (int i = L; i < PW; i += SIG2_LANES) {
     const int64_t gi = pw0 + i;
     pk[i] = (gi >= 0 && (uint64_t)gi < a.n_pwords) ? a.packed[gi] : 0ull;
   }
-  for (int i = L; i < SIG2_MWORDS; i += SIG2_LANES) {
+  for (int i = L; i < MW; i += SIG2_LANES) {
     const int64_t gi = mw0 + i;
     const bool in = gi >= 0 && (uint64_t)gi < a.n_mwords;
     const uint64_t x = in ? a.inval[gi] : ~0ull, y = in ? a.smask[gi] : 0ull;
@@ -475,10 +480,10 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   if (L < 32) {
     // last read start strictly before each staged mask word (prefix max)
     int64_t carry = rs0;
-    for (int base = 0; base < SIG2_MWORDS; base += 32) {
+    for (int base = 0; base < MW; base += 32) {
       const int i = base + L;
       int64_t here = -1;
-      if (i < SIG2_MWORDS && sm[i]) here = LBm + (int64_t)i * 64 + 64 - __ffsll((long long)sm[i]);
+      if (i < MW && sm[i]) here = LBm + (int64_t)i * 64 + 64 - __ffsll((long long)sm[i]);
       int64_t v = here;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
       }
       int64_t excl = __shfl_up_sync(FULL, v, 1);
       if (L == 0) excl = -1;
-      if (i < SIG2_MWORDS) lastw[i] = excl > carry ? excl : carry;
+      if (i < MW) lastw[i] = excl > carry ? excl : carry;
       const int64_t tot = __shfl_sync(FULL, v, 31);
       if (tot > carry) carry = tot;
     }
@@ -829,12 +834,13 @@ __global__ void map_assign_kernel(const uint64_t *keys, const uint64_t *prefix, 
   }
 }
 
-// The same map without a sort, for up to MAP_DIRECT_MAX signatures: the
+// The same map without a sort, for up to MAP_DIRECT_MAX signatures (m <= 7:
+// 4^m m-mers and the sentinel): the
 // weight preceding signature s in the order above is summed directly,
 // W(s) = sum of w(t) over the t with w(t) > w(s), or w(t) = w(s) and t < s
 // (weights clamped to 32 bits as in the sort key).  CTA (x, y) takes
 // signatures [256x, 256x + 256) against the y-th slice of all signatures.
-constexpr uint32_t MAP_DIRECT_MAX = 16384;
+constexpr uint32_t MAP_DIRECT_MAX = (1u << 14) + 1u;
 constexpr int MAP_DIRECT_SLICES = 16;
 __global__ void __launch_bounds__(256) map_prefix_kernel(const unsigned long long *__restrict__ w, uint32_t n_sig,
                                                          unsigned long long *__restrict__ before,
