@@ -852,20 +852,19 @@ struct TileHashSmem {
   static constexpr int SLOTS = HASH_SLOTS;
   unsigned long long tk[SLOTS];    // slot keys (kHashEmpty when free)
   uint32_t tc[SLOTS];              // slot counts
-  uint64_t ws64[THREADS / 32 + 1];
-  unsigned long long base;
-  unsigned long long start;        // the next tile: first key, index, keys, group
-  uint32_t t, n, group;
+  unsigned long long start[2];     // tiles, alternately: first key, index, keys, group
+  uint32_t t[2], n[2], group[2];
 };
 
 // Thread 0: claims the next tile that fits (bigger ones go to the big list)
-// and records it in s.start/t/n/group (t = number of tiles when none is left).
+// and records it in slot q of s.start/t/n/group (t = number of tiles when
+// none is left).
 template <typename SM>
-__device__ void hash_claim(SM &s, const TilePlan &plan, uint32_t nt, uint32_t *work, uint32_t *big_list,
+__device__ void hash_claim(SM &s, int q, const TilePlan &plan, uint32_t nt, uint32_t *work, uint32_t *big_list,
                            uint32_t *n_big, unsigned long long *big_keys, uint32_t big_cap, uint32_t *err) {
   for (;;) {
     const uint32_t t = atomicAdd(work, 1u);
-    s.t = t;
+    s.t[q] = t;
     if (t >= nt) return;
     const TileDesc d = plan.desc[t];
     if (d.n == 0) continue;
@@ -873,13 +872,17 @@ __device__ void hash_claim(SM &s, const TilePlan &plan, uint32_t nt, uint32_t *w
       push_big(t, d.n, big_list, n_big, big_keys, big_cap, err);
       continue;
     }
-    s.start = d.st;
-    s.n = d.n;
-    s.group = d.group;
+    s.start[q] = d.st;
+    s.n[q] = d.n;
+    s.group[q] = d.group;
     return;
   }
 }
 
+// Two barriers per tile: inserts | emission (which also clears the slots
+// for the next tile) |.  Each warp reserves its survivors' places with one
+// global atomic, so no block-wide scan is needed; the tile record is double
+// buffered so that thread 0 claims the next tile while this one is counted.
 template <int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS, 3)
 tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *work, CountOut<uint64_t> out,
@@ -892,22 +895,24 @@ tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *wor
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const uint32_t nt = *plan.n_tiles;
   const int tid = threadIdx.x;
-  if (tid == 0) hash_claim(s, plan, nt, work, big_list, n_big, big_keys, big_cap, err);
-  __syncthreads();
-  for (;;) {
-    if (s.t >= nt) break;
-    const int n = (int)s.n;
-    const uint64_t *src = keys + s.start;
-    const uint32_t group = s.group;
-    // clear the table (thread t owns slots t, t + THREADS, ...)
+  const unsigned lane = lane_id();
+  // clear the table (thread t owns slots t, t + THREADS, ...)
 #pragma unroll
-    for (int q = 0; q < SPT; ++q) {
-      s.tk[q * THREADS + tid] = kHashEmpty;
-      s.tc[q * THREADS + tid] = 0;
-    }
-    __syncthreads();  // table clear; the tile's record has been read by all
+  for (int q = 0; q < SPT; ++q) {
+    s.tk[q * THREADS + tid] = kHashEmpty;
+    s.tc[q * THREADS + tid] = 0;
+  }
+  if (tid == 0) hash_claim(s, 0, plan, nt, work, big_list, n_big, big_keys, big_cap, err);
+  __syncthreads();
+  unsigned long long n_distinct = 0;
+  for (int it = 0;; ++it) {
+    const int cur = it & 1;
+    if (s.t[cur] >= nt) break;
+    const int n = (int)s.n[cur];
+    const uint64_t *src = keys + s.start[cur];
+    const uint32_t group = s.group[cur];
     // the next tile is claimed while this one is counted
-    if (tid == 0) hash_claim(s, plan, nt, work, big_list, n_big, big_keys, big_cap, err);
+    if (tid == 0) hash_claim(s, cur ^ 1, plan, nt, work, big_list, n_big, big_keys, big_cap, err);
     uint64_t key[IPT];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -927,40 +932,42 @@ tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *wor
       atomicAdd(&s.tc[h], 1u);
     }
     __syncthreads();
-    // occupied slots are the tile's distinct keys
-    uint32_t n_groups = 0, n_keep = 0;
+    // occupied slots are the tile's distinct keys; read and clear them
+    uint32_t keep = 0;  // bit q: slot q * THREADS + tid survives
+    uint32_t cc[SPT];
 #pragma unroll
     for (int q = 0; q < SPT; ++q) {
-      const uint32_t c = s.tc[q * THREADS + tid];
-      n_groups += c != 0;
-      n_keep += c >= out.ci && c <= out.cx;
+      cc[q] = s.tc[q * THREADS + tid];
+      n_distinct += cc[q] != 0;
+      if (cc[q] >= out.ci && cc[q] <= out.cx) keep |= 1u << q;  // ci >= 1
     }
-    uint64_t tot2;
-    const uint64_t pre = block_excl_scan<uint64_t, THREADS>(((uint64_t)n_groups << 32) | n_keep, s.ws64, &tot2);
-    uint32_t kb = (uint32_t)pre;
-    const uint32_t ktot = (uint32_t)tot2;
-    if (tid == 0) {
-      s.base = ktot ? atomicAdd(out.n, (unsigned long long)ktot) : 0ull;
-      atomicAdd(out.n_distinct, tot2 >> 32);
-    }
-    __syncthreads();
-    const uint64_t base = s.base;
-    if (base + ktot > out.cap) {
-      if (tid == 0) atomicOr(err, ERR_CAPACITY);
-    } else if (n_keep) {
+    const uint32_t nk = (uint32_t)__popc(keep);
+    const uint32_t incl = warp_incl_scan(nk);
+    const uint32_t wtot = __shfl_sync(FULL, incl, 31);
+    unsigned long long wbase = 0;
+    if (lane == 31 && wtot) wbase = atomicAdd(out.n, (unsigned long long)wtot);
+    wbase = __shfl_sync(FULL, wbase, 31);
+    const bool fits = wbase + wtot <= out.cap;
+    if (!fits && lane == 0) atomicOr(err, ERR_CAPACITY);
+    uint64_t p = wbase + incl - nk;
 #pragma unroll
-      for (int q = 0; q < SPT; ++q) {
-        const uint32_t c = s.tc[q * THREADS + tid];
-        if (c >= out.ci && c <= out.cx) {
-          out.keys[base + kb] = out.mixer.unmix(s.tk[q * THREADS + tid]);
-          out.counts[base + kb] = c;
-          if (out.slots) out.slots[base + kb] = group / out.bins_per_slot;
-          ++kb;
+    for (int q = 0; q < SPT; ++q) {
+      if (cc[q]) {
+        const int e = q * THREADS + tid;
+        if (fits && ((keep >> q) & 1u)) {
+          out.keys[p] = out.mixer.unmix(s.tk[e]);
+          out.counts[p] = cc[q];
+          if (out.slots) out.slots[p] = group / out.bins_per_slot;
+          ++p;
         }
+        s.tk[e] = kHashEmpty;
+        s.tc[e] = 0;
       }
     }
-    __syncthreads();  // the table is read above before the next tile clears it
+    __syncthreads();  // the slots are clear and the next tile is claimed
   }
+  const unsigned long long nd = __reduce_add_sync(FULL, (unsigned)n_distinct);
+  if (lane == 0 && nd) atomicAdd(out.n_distinct, nd);
 }
 
 // Pairs mode: sort every tile of (key, value) pairs in place (keys/vals are
