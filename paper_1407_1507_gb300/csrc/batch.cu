@@ -239,7 +239,7 @@ struct BatchEngine {
     // kernel attributes and occupancies are set here, outside any capture
     KMC_CUDA_TRY(sig_prepare());
     KMC_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(ScatSmem)));
+                                      (int)scat_smem_bytes(SIG_SMEM_BINS)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_scatter_kernel<uint64_t>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sizeof(KxScatterSmem<uint64_t>)));
@@ -459,7 +459,7 @@ int BatchEngine::sequence() {
   auto *cur = as<unsigned long long>(cursors);
   KMC_CUDA_TRY(cudaMemcpyAsync(cur, rec_base.p, (size_t)B_total * 8, cudaMemcpyDeviceToDevice, st));
   KMC_CUDA_TRY(cudaMemcpyAsync(cur + B_total, word_base.p, (size_t)B_total * 8, cudaMemcpyDeviceToDevice, st));
-  scatter_kernel<<<gfor(list_cap, SCAT_PER_CTA), SCAT_THREADS, sizeof(ScatSmem), st>>>(
+  scatter_kernel<<<gfor(list_cap, SCAT_PER_CTA), SCAT_THREADS, scat_smem_bytes(B_total), st>>>(
       as<uint64_t>(list), 0, as<uint32_t>(map), B_total, k, as<uint64_t>(packed), cur, cur + B_total,
       as<uint64_t>(index), as<uint64_t>(words), &d->n_list, as<uint64_t>(set_starts), max_sets, tune.bins);
   KMC_COUNT_LAUNCH();

@@ -41,7 +41,7 @@ constexpr int SIG_NPK = (SIG_NMM + 64 + 64) / 32 + 4;  // packed words staged
 constexpr int SIG_NMK = (SIG_NMM + 64 + 64) / 64 + 4;  // mask words staged
 constexpr int SIG_SMEM_BINS = 2048;                  // per-bin histograms kept in smem up to this
 constexpr int SCAT_THREADS = 256;
-constexpr int SCAT_PER_CTA = 2048;
+constexpr int SCAT_PER_CTA = 1024;
 constexpr int STREAM_PAD_WORDS = 8;                  // zero / invalid words after a stream
 
 // ------------------------------------------------------------------ a1
@@ -725,15 +725,30 @@ inline int sig_launch(const SigArgs &a, uint64_t n_stream, bool tile, cudaStream
 
 // ------------------------------------------------------------------ a3
 
+// Per-CTA scratch of the bin scatter: the record table, the word slots and,
+// after it, the per-bin counters and bases for hb bins (hb = n_bins when
+// n_bins <= SIG_SMEM_BINS, else 0).
+constexpr int SCAT_WCAP = SCAT_PER_CTA * 5;  // word slots (records of up to 5 words on average)
 struct ScatSmem {
-  uint32_t c_rec[SIG_SMEM_BINS], c_words[SIG_SMEM_BINS];
-  unsigned long long b_rec[SIG_SMEM_BINS], b_words[SIG_SMEM_BINS];
+  unsigned long long wi[SCAT_PER_CTA];   // first destination word of each record
+  uint32_t pos[SCAT_PER_CTA];            // stream position of each record
+  uint32_t wofs[SCAT_PER_CTA];           // first word slot of each record (nw before the scan)
+  uint16_t nbits[SCAT_PER_CTA];          // bits of each record
+  uint16_t wrec[SCAT_WCAP];              // record of each word slot
+  uint32_t ws[SCAT_THREADS / 32 + 1];
 };
+inline size_t scat_smem_bytes(uint32_t n_bins) {
+  const size_t hb = n_bins <= (uint32_t)SIG_SMEM_BINS ? n_bins : 0;
+  return ((sizeof(ScatSmem) + 15) & ~(size_t)15) + hb * 24;
+}
 
 // Scatters super k-mer records into their bins: an index entry (word
 // offset | n_kmers-1 | signature) and the packed bases (Sect. 2.4: super
 // k-mers are sent to bins).  Space is reserved per CTA and bin with one
 // global atomic per non-empty bin (per record when there are many bins).
+// The bases are copied one word per thread over the CTA's word slots in
+// record order, so that neighbouring threads read neighbouring words and
+// all loads of a thread are independent.
 __global__ void __launch_bounds__(SCAT_THREADS)
 scatter_kernel(const uint64_t *__restrict__ list, uint64_t n_list, const uint32_t *__restrict__ map,
                uint32_t n_bins, int k, const uint64_t *__restrict__ packed,
@@ -744,66 +759,123 @@ scatter_kernel(const uint64_t *__restrict__ list, uint64_t n_list, const uint32_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatSmem &s = *reinterpret_cast<ScatSmem *>(smem_raw);
   const bool small_bins = n_bins <= (uint32_t)SIG_SMEM_BINS;
+  const uint32_t hb = small_bins ? n_bins : 0u;
+  uint32_t *c_rec = reinterpret_cast<uint32_t *>(smem_raw + ((sizeof(ScatSmem) + 15) & ~(size_t)15));
+  uint32_t *c_words = c_rec + hb;
+  unsigned long long *b_rec = reinterpret_cast<unsigned long long *>(c_words + hb);  // 8-byte aligned
+  unsigned long long *b_words = b_rec + hb;
   const uint64_t c0 = (uint64_t)blockIdx.x * SCAT_PER_CTA;
   if (n_list_dyn) {
     n_list = *n_list_dyn;
     if (c0 >= n_list) return;
   }
+  const uint32_t n_here = (uint32_t)(n_list - c0 < (uint64_t)SCAT_PER_CTA ? n_list - c0 : (uint64_t)SCAT_PER_CTA);
   constexpr int PER = SCAT_PER_CTA / SCAT_THREADS;
+  const int tid = threadIdx.x;
   uint64_t rec[PER];
   uint32_t bin[PER], nw[PER];
-  if (small_bins) {
-    for (int i = threadIdx.x; i < (int)n_bins; i += SCAT_THREADS) s.c_rec[i] = s.c_words[i] = 0;
-    __syncthreads();
-  }
+  for (uint32_t i = tid; i < hb; i += SCAT_THREADS) c_rec[i] = c_words[i] = 0;
+  __syncthreads();
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const uint64_t i = c0 + (uint64_t)q * SCAT_THREADS + threadIdx.x;
-    rec[q] = i < n_list ? list[i] : ~0ull;
-    if (i < n_list) {
+    const uint32_t e = (uint32_t)q * SCAT_THREADS + tid;
+    rec[q] = e < n_here ? list[c0 + e] : ~0ull;
+    nw[q] = 0;
+    if (e < n_here) {
       const uint32_t n = (uint32_t)((rec[q] >> 25) & 127u) + 1;
       bin[q] = slot_of(set_starts, n_slots, rec[q] >> 32) * bins_per_slot + map[rec[q] & 0x1FFFFFFu];
       nw[q] = (2 * (n + k - 1) + 63) / 64;
       if (small_bins) {
-        atomicAdd(&s.c_rec[bin[q]], 1u);
-        atomicAdd(&s.c_words[bin[q]], nw[q]);
+        atomicAdd(&c_rec[bin[q]], 1u);
+        atomicAdd(&c_words[bin[q]], nw[q]);
       }
     }
   }
   if (small_bins) {
     __syncthreads();
-    for (int i = threadIdx.x; i < (int)n_bins; i += SCAT_THREADS) {
-      if (s.c_rec[i]) {
-        s.b_rec[i] = atomicAdd(&rec_cursor[i], (unsigned long long)s.c_rec[i]);
-        s.b_words[i] = atomicAdd(&word_cursor[i], (unsigned long long)s.c_words[i]);
+    for (uint32_t i = tid; i < hb; i += SCAT_THREADS) {
+      if (c_rec[i]) {
+        b_rec[i] = atomicAdd(&rec_cursor[i], (unsigned long long)c_rec[i]);
+        b_words[i] = atomicAdd(&word_cursor[i], (unsigned long long)c_words[i]);
       }
-      s.c_rec[i] = 0;
-      s.c_words[i] = 0;
+      c_rec[i] = 0;
+      c_words[i] = 0;
     }
     __syncthreads();
   }
+  // index entries, and the record table for the word copy
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const uint64_t i = c0 + (uint64_t)q * SCAT_THREADS + threadIdx.x;
-    if (i >= n_list) continue;
+    const uint32_t e = (uint32_t)q * SCAT_THREADS + tid;
+    if (e >= n_here) continue;
     uint64_t ri, wi;
     if (small_bins) {
-      ri = s.b_rec[bin[q]] + atomicAdd(&s.c_rec[bin[q]], 1u);
-      wi = s.b_words[bin[q]] + atomicAdd(&s.c_words[bin[q]], nw[q]);
+      ri = b_rec[bin[q]] + atomicAdd(&c_rec[bin[q]], 1u);
+      wi = b_words[bin[q]] + atomicAdd(&c_words[bin[q]], nw[q]);
     } else {
       ri = atomicAdd(&rec_cursor[bin[q]], 1ull);
       wi = atomicAdd(&word_cursor[bin[q]], (unsigned long long)nw[q]);
     }
-    const uint64_t pos = rec[q] >> 32;
     const uint32_t n = (uint32_t)((rec[q] >> 25) & 127u) + 1;
-    const uint32_t nbits = 2 * (n + k - 1);
-    for (uint32_t j = 0; j < nw[q]; ++j) {
-      uint64_t v = get_bits(packed, 2 * pos + 64ull * j, 64);
-      const uint32_t used = nbits - 64 * j;
-      if (used < 64) v &= ~0ull << (64 - used);
-      words[wi + j] = v;
-    }
     index[ri] = (wi << 32) | (rec[q] & 0xFFFFFFFFull);
+    s.wi[e] = wi;
+    s.pos[e] = (uint32_t)(rec[q] >> 32);
+    s.nbits[e] = (uint16_t)(2 * (n + k - 1));
+    s.wofs[e] = nw[q];
+  }
+  __syncthreads();
+  // word slots: exclusive scan of the records' word counts in record order
+  // (thread t scans records PER t .. PER t + PER - 1)
+  uint32_t W;
+  {
+    uint32_t c[PER], sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const uint32_t e = (uint32_t)PER * tid + j;
+      c[j] = e < n_here ? s.wofs[e] : 0u;
+      sum += c[j];
+    }
+    uint32_t run = block_excl_scan<uint32_t, SCAT_THREADS>(sum, s.ws, &W);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const uint32_t e = (uint32_t)PER * tid + j;
+      if (e < n_here) s.wofs[e] = run;
+      run += c[j];
+    }
+  }
+  __syncthreads();
+  if (W <= (uint32_t)SCAT_WCAP) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const uint32_t e = (uint32_t)q * SCAT_THREADS + tid;
+      if (e < n_here)
+        for (uint32_t j = 0; j < nw[q]; ++j) s.wrec[s.wofs[e] + j] = (uint16_t)e;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (uint32_t i = tid; i < W; i += SCAT_THREADS) {
+      const uint32_t e = s.wrec[i];
+      const uint32_t j = i - s.wofs[e];
+      uint64_t v = get_bits(packed, 2ull * s.pos[e] + 64ull * j, 64);
+      const uint32_t used = (uint32_t)s.nbits[e] - 64 * j;
+      if (used < 64) v &= ~0ull << (64 - used);
+      words[s.wi[e] + j] = v;
+    }
+  } else {
+    // more words than slots: each thread copies its own records
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const uint32_t e = (uint32_t)q * SCAT_THREADS + tid;
+      if (e >= n_here) continue;
+      const uint64_t wi = s.wi[e];
+      const uint32_t nbits = s.nbits[e];
+      for (uint32_t j = 0; j < nw[q]; ++j) {
+        uint64_t v = get_bits(packed, 2ull * s.pos[e] + 64ull * j, 64);
+        const uint32_t used = nbits - 64 * j;
+        if (used < 64) v &= ~0ull << (64 - used);
+        words[wi + j] = v;
+      }
+    }
   }
 }
 

@@ -236,12 +236,12 @@ int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_
     static bool attr_set = false;
     if (!attr_set) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(ScatSmem)));
+                                        (int)scat_smem_bytes(SIG_SMEM_BINS)));
       attr_set = true;
     }
     StageScope sc(h, KMC_STAGE_BIN_SCATTER);
     scatter_kernel<<<(unsigned)((n_rec + SCAT_PER_CTA - 1) / SCAT_PER_CTA), SCAT_THREADS,
-                     sizeof(ScatSmem), h.st>>>(as<uint64_t>(ds.list), n_rec, as<uint32_t>(h.map), B,
+                     scat_smem_bytes(B), h.st>>>(as<uint64_t>(ds.list), n_rec, as<uint32_t>(h.map), B,
                                                (int)h.p.k, as<uint64_t>(ds.packed), h_rec, h_words,
                                                static_cast<uint64_t *>(pc->index.p),
                                                static_cast<uint64_t *>(pc->words.p)); KMC_COUNT_LAUNCH();
