@@ -26,7 +26,7 @@ Mixer<K> make_mixer(int key_bits) {
   m.bits = key_bits;
   m.mask = key_bits >= (int)(8 * sizeof(K)) ? ~K(0) : ((K(1) << key_bits) - 1);
   K c = (K)0x9E3779B97F4A7C15ull;
-  if (sizeof(K) > 8) c = (c << 64) | (K)0xD1B54A32D192ED03ull;
+  if constexpr (sizeof(K) > 8) c = (c << 64) | (K)0xD1B54A32D192ED03ull;
   c |= 1;
   K inv = c;  // Newton iteration for the inverse modulo 2^(8 sizeof K)
   for (int i = 0; i < 7; ++i) inv *= K(2) - c * inv;

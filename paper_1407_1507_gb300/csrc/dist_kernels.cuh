@@ -374,11 +374,11 @@ __global__ void __launch_bounds__(SIG_THREADS) sig_kernel(SigArgs a) {
 // shared-memory row; the minimum over the window [p, p+w-1] is then the
 // smaller of the suffix minimum of p's block (from p) and the prefix minimum
 // of the next block (to p+w-1): van Herk / Gil-Werman with block size w.
-// The last lane only lends its prefix minima, so a CTA covers 127*w positions,
+// The last lane only lends its prefix minima, so a CTA covers (lanes-1)*w positions,
 // starting one position before the k-mer starts it owns and extending
 // kSuperkmerCap past them (a super k-mer never spans more).
 
-constexpr int SIG2_LANES = 128;
+constexpr int SIG2_LANES = 256;
 constexpr int SIG2_MAXW = 64;
 // Mask words staged per CTA (the lanes' blocks, the k-1 positions after
 // them, alignment); twice as many packed words (32 bases each) are staged.

@@ -10,7 +10,7 @@ namespace kmc {
 namespace {
 
 constexpr int KX_THREADS = 256;
-constexpr int KX_RECORDS_PER_CHUNK = 512;
+constexpr int KX_RECORDS_PER_CHUNK = 1024;
 constexpr int CNT_THREADS = 256;
 constexpr int CNT_IPT64 = 16;   // tile = 4096 64-bit keys
 constexpr int CNT_IPT128 = 8;   // tile = 2048 128-bit keys

@@ -484,7 +484,7 @@ tile_count_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &sm = *reinterpret_cast<SM *>(smem_raw);
   const uint32_t nt = *plan.n_tiles;
-  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  const unsigned lane = lane_id();
   for (;;) {
     const uint32_t t = next_tile(work, &sm.tile);
     if (t >= nt) break;
@@ -989,7 +989,7 @@ tile_pairs_kernel(K *keys, V *vals, TilePlan plan, uint32_t *work, uint32_t *big
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &sm = *reinterpret_cast<SM *>(smem_raw);
   const uint32_t nt = *plan.n_tiles;
-  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  const unsigned lane = lane_id();
   for (;;) {
     const uint32_t t = next_tile(work, &sm.tile);
     if (t >= nt) break;
