@@ -162,6 +162,13 @@ def cpu_baseline(w, k, ci, cx):
 
 # Algorithmic bytes per launch of each stage (minimum traffic of the method:
 # every input read once, every output written once).
+# DRAM bytes (read + written) per key of the two sweeps (kx0_sweep_kernel on
+# 64-bit keys, both modes), from one ncu capture of the 1 M-read case
+# (--scale 0.05: 3,747.6 MB for 119,586,137 keys); the sweeps' traffic grows
+# with the keys, so it is scaled by this run's keys.
+SWEEP_DRAM_BYTES_PER_KEY_U64 = 3747.6e6 / 119586137
+
+
 def stage_bytes(st, k):
     nb = st["n_bases"]
     npos = st["n_kmer_positions"]
@@ -248,8 +255,11 @@ def run_ours(args, rank, local_rank, world):
             stages[s].update({"alg_bytes": int(alg[s]), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
     stages["sum_ms"] = round(sum(per.values()), 3)
     achieved = stages[dom]["gbs"]
+    traffic = None
+    if dom == "kx_scatter" and k <= 32 and st0.get("x_used", 0) == 0:
+        traffic = int(SWEEP_DRAM_BYTES_PER_KEY_U64 * st0["n_kmer_positions"])
     roofline = {"bound": "hbm", "kernel_stage": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
 
     # end to end through the public API with host (pinned) buffers
@@ -278,12 +288,16 @@ def run_ours(args, rank, local_rank, world):
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        laps = []
         for _ in range(args.steps):
-            e2e_step()
+            t1 = time.perf_counter()
+            e2e_step()  # ends with the result read back into host memory
+            laps.append((time.perf_counter() - t1) * 1e3)
         torch.cuda.synchronize(dev)
         barrier()
         e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
         e2e = {"value": job_rate(npos, world, e_ms), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+               "ms_per_step_median": round(float(np.median(laps)), 3), "ms_per_step_max": round(max(laps), 3),
                "h2d_bytes_per_step": int(w.bases.size + w.offsets.size * 8),
                "d2h_bytes_per_step": int(nout * (8 * words + 4))}
     kmc.kmc_close(h)
