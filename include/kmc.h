@@ -48,6 +48,8 @@ extern "C" {
 #define KMC_ETIMEOUT (-7)  /* a device-side bounded wait gave up            */
 #define KMC_EAGAIN (-8)    /* not ready yet (server poll)                   */
 #define KMC_EINPUT (-9)    /* malformed read offsets                         */
+#define KMC_EIO (-10)      /* a database file cannot be read or written, or
+                              is not in the KMC 2 format                    */
 
 #define KMC_AUTO 0xFFFFFFFFu
 #define KMC_MAX_K 64u
@@ -214,6 +216,62 @@ const char *kmc_strerror(int code);
  * KMC_ESTATE. */
 int kmc_set_bin_map(kmc_handle *h, const uint32_t *map, uint64_t n_entries);
 int kmc_get_bin_map(const kmc_handle *h, uint32_t *map, uint64_t n_entries);
+
+/* ---------------------------------------------------------- database
+ * KMC 2's output database (Suppl. "Database format"): two files, <path>.kmc_pre
+ * and <path>.kmc_suf, integers least significant byte first.
+ *
+ * .kmc_pre: "KMCP"; the prefix arrays, one per bin in bin order, each of
+ * 4^lut uint64 (element x = index of the bin's first record whose first lut
+ * symbols have value x), then one uint64 guard (the number of records); the
+ * map, 4^m + 1 uint32 (signature -> bin, the map kmc_count used); the header
+ * (kmer_length, mode = 0, counter_size, lut_prefix_length, signature_length,
+ * min_count, max_count as uint32, total_kmers as uint64, seven unused uint32
+ * written as 0, KMC_VER = 0x200 as uint32: 68 bytes); the header's size
+ * (uint32, so that the header starts that many + 8 bytes before the end);
+ * "KMCP".  .kmc_suf: "KMCS"; one record per k-mer, grouped by bin and ordered
+ * by k-mer value inside a bin: the last k - lut symbols of the canonical
+ * k-mer, four per byte, first symbol in the top bits, then the count on
+ * counter_size bytes; "KMCS".  Where the format leaves a choice:
+ * lut = (k mod 4) + 4 when that is at most k and n_bins * 4^lut <= 2^24, else
+ * k mod 4; counter_size = the fewest bytes holding the largest count;
+ * min_count = max(cutoff_min, 1), max_count = min(cutoff_max, 2^32 - 1).
+ *
+ * kmc_db_write: after kmc_count, writes the result of the handle; the
+ * records and prefix arrays are built on the device (each k-mer's
+ * signature, Sect. 2.2, picks its bin through the map).  path is the common
+ * prefix of the two file names.  Errors: KMC_ESTATE (before kmc_count),
+ * KMC_EIO (a file cannot be written), KMC_ENOMEM, KMC_ECUDA.
+ *
+ * kmc_db_open: reads a database with the format section's procedure (both
+ * markers, the header position, the header, the map and prefix arrays, the
+ * records) and loads it into the memory of CUDA device `device`.  Errors:
+ * KMC_EIO (missing, truncated or malformed file; nothing is allocated),
+ * KMC_EINVAL, KMC_ENOMEM, KMC_ECUDA.
+ *
+ * kmc_db_lookup: counts of n query k-mers, as the format section looks one
+ * up: the canonical form (Sect. 2.1), its signature, the map, the prefix
+ * array range, a binary search over the suffixes; 0 for a k-mer that is not
+ * in the database.  d_kmers (device memory) holds n * ceil(k/32) words, laid
+ * out as in kmc_result (bits above 2k are ignored; either strand); d_counts
+ * (device memory) receives n uint32.  Runs on cuda_stream (NULL: the legacy
+ * default stream) and returns without waiting.  Errors: KMC_EINVAL.
+ *
+ * kmc_db_info_get fills the header fields; kmc_db_close releases the
+ * database (NULL is a no-op). */
+typedef struct kmc_db kmc_db;
+typedef struct {
+  uint32_t kmer_length, mode, counter_size, lut_prefix_length, signature_length;
+  uint32_t min_count, max_count;
+  uint64_t total_kmers;
+  uint32_t kmc_ver;
+  uint32_t n_arrays; /* prefix arrays (bins) */
+} kmc_db_info;
+int kmc_db_write(kmc_handle *h, const char *path);
+int kmc_db_open(kmc_db **db, const char *path, int device);
+int kmc_db_info_get(const kmc_db *db, kmc_db_info *info);
+int kmc_db_lookup(kmc_db *db, const uint64_t *d_kmers, uint64_t n, uint32_t *d_counts, void *cuda_stream);
+void kmc_db_close(kmc_db *db);
 
 /* ---------------------------------------------------------- introspection
  * Intermediate results, for checking each step against a CPU restatement.

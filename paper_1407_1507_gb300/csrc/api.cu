@@ -42,19 +42,6 @@ cudaMemPool_t pool_for(int dev) {
   return pools[dev];
 }
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 __global__ void find_bounds_kernel(const uint64_t *offsets, uint64_t n_reads, const uint64_t *targets,
                                    uint32_t n_t, uint64_t *out_read, uint64_t *out_off) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -356,11 +343,11 @@ int add_pinned(Handle &h, const char *bases, const uint64_t *offsets, uint64_t n
 }  // namespace
 }  // namespace kmc
 
-using namespace kmc;
+namespace kmc {
+void set_error_text(const char *msg) { snprintf(g_last_err, sizeof(g_last_err), "%s", msg); }
+}  // namespace kmc
 
-struct kmc_handle {
-  Handle h;
-};
+using namespace kmc;
 
 extern "C" {
 
@@ -390,6 +377,7 @@ const char *kmc_strerror(int code) {
     case KMC_ETIMEOUT: return "device-side wait timed out";
     case KMC_EAGAIN: return "not ready";
     case KMC_EINPUT: return "malformed read offsets";
+    case KMC_EIO: return g_last_err[0] ? g_last_err : "file error";
     default: return "unknown error";
   }
 }

@@ -10,6 +10,20 @@
 namespace kmc {
 
 int cuda_fail(cudaError_t e, const char *what);
+void set_error_text(const char *msg);  // the text kmc_strerror gives for KMC_EIO
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 extern thread_local uint64_t g_launches;
 
 // Stream-ordered device buffer that only grows (reused across calls).
@@ -166,3 +180,8 @@ int sort_pairs_u128(Handle &h, unsigned __int128 *keys, uint32_t *vals, uint64_t
 int check_device_error(Handle &h);
 
 }  // namespace kmc
+
+// The object behind the C ABI's kmc_handle.
+struct kmc_handle {
+  kmc::Handle h;
+};

@@ -25,6 +25,7 @@ KMC_ETRUNC = -6
 KMC_ETIMEOUT = -7
 KMC_EAGAIN = -8
 KMC_EINPUT = -9
+KMC_EIO = -10
 KMC_AUTO = 0xFFFFFFFF
 KMC_DEBUG_KEEP_SUPERKMERS = 1
 KMC_DEBUG_KEEP_KEYS = 2
@@ -106,6 +107,18 @@ KMC_BATCH_AUTOTUNE = 1
 KMC_BATCH_NO_GRAPH = 2
 
 
+class kmc_db_info(ctypes.Structure):
+    _fields_ = [
+        ("kmer_length", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("counter_size", ctypes.c_uint32),
+        ("lut_prefix_length", ctypes.c_uint32), ("signature_length", ctypes.c_uint32),
+        ("min_count", ctypes.c_uint32), ("max_count", ctypes.c_uint32), ("total_kmers", ctypes.c_uint64),
+        ("kmc_ver", ctypes.c_uint32), ("n_arrays", ctypes.c_uint32),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class KmcError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"{what}: {strerror(code)} ({code})")
@@ -151,6 +164,11 @@ SIGNATURES = [
     ("kmc_server_release", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("kmc_server_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_server_stats)]),
     ("kmc_server_close", None, [_vp]),
+    ("kmc_db_write", ctypes.c_int, [_vp, ctypes.c_char_p]),
+    ("kmc_db_open", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_char_p, ctypes.c_int]),
+    ("kmc_db_info_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_db_info)]),
+    ("kmc_db_lookup", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, _vp, _vp]),
+    ("kmc_db_close", None, [_vp]),
     ("kmc_count_small_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64,
                                                _vp, _vp]),
@@ -303,6 +321,34 @@ def kmc_debug_bin_keys(h, b: int):
     _check(load().kmc_debug_bin_keys(h, b, _ptr(keys, ctypes.c_uint64), n.value, ctypes.byref(n),
                                      ctypes.byref(w)), "kmc_debug_bin_keys")
     return keys[:n.value]
+
+
+def kmc_db_write(h, path: str):
+    """Writes <path>.kmc_pre and <path>.kmc_suf from the counted result."""
+    _check(load().kmc_db_write(h, os.fsencode(path)), "kmc_db_write")
+
+
+def kmc_db_open(path: str, device: int = 0) -> int:
+    db = _vp()
+    _check(load().kmc_db_open(ctypes.byref(db), os.fsencode(path), device), "kmc_db_open")
+    return db.value
+
+
+def kmc_db_info_get(db) -> dict:
+    info = kmc_db_info()
+    _check(load().kmc_db_info_get(db, ctypes.byref(info)), "kmc_db_info_get")
+    return info.as_dict()
+
+
+def kmc_db_lookup(db, d_kmers_ptr: int, n: int, d_counts_ptr: int, stream=None):
+    """Counts of n device-resident query k-mers into a device uint32 array;
+    asynchronous on `stream` (a cudaStream_t value, None: legacy default)."""
+    _check(load().kmc_db_lookup(db, d_kmers_ptr, n, d_counts_ptr, stream), "kmc_db_lookup")
+
+
+def kmc_db_close(db):
+    if db:
+        load().kmc_db_close(db)
 
 
 KMC_NOALLOC_MAX_BASES = 1 << 20
@@ -462,6 +508,14 @@ class Counter:
 
     def stats(self):
         return kmc_stats_get(self.h)
+
+    def bin_map(self):
+        return kmc_get_bin_map(self.h, 4 ** self.stats()["m_used"] + 1)
+
+    def write_db(self, path):
+        """KMC 2 database files <path>.kmc_pre / <path>.kmc_suf of the result."""
+        kmc_db_write(self.h, path)
+        return self
 
     def close(self):
         kmc_close(self.h)

@@ -56,7 +56,7 @@ def test_default_params_are_the_papers(lib):
 
 
 def test_strerror_names_every_code(lib):
-    for code in range(0, -10, -1):
+    for code in range(0, -11, -1):
         s = kmc.strerror(code)
         assert s and s != "unknown error"
 
@@ -84,3 +84,33 @@ def test_null_handles_are_rejected(lib):
     assert lib.kmc_count(None) == kmc.KMC_EINVAL
     assert lib.kmc_result_size(None, ctypes.byref(n)) == kmc.KMC_EINVAL
     lib.kmc_close(None)  # no-op
+
+
+def test_db_open_rejects_missing_and_malformed_files(lib, tmp_path):
+    """The reader checks the format section's markers, header position and
+    sizes before touching a device, so malformed files fail on the host."""
+    from oracle import kmc_db as DB
+    from oracle import strings as S
+    reads = ["ACGTTGCAACGGTTACGATCGATCGGATCCA", "TTGCAACGGTTACGATCGAT"]
+    cnt = S.count_brute(reads, 12, 1)
+    pre, suf = DB.write(12, 5, [S.value(x) for x in cnt], list(cnt.values()), [0] * (4 ** 5 + 1), 1, 1, 10 ** 9)
+    db = ctypes.c_void_p()
+
+    def open_with(p_bytes, s_bytes, name):
+        base = str(tmp_path / name)
+        if p_bytes is not None:
+            open(base + ".kmc_pre", "wb").write(p_bytes)
+        if s_bytes is not None:
+            open(base + ".kmc_suf", "wb").write(s_bytes)
+        return lib.kmc_db_open(ctypes.byref(db), os.fsencode(base), 0)
+
+    assert open_with(None, None, "missing") == kmc.KMC_EIO
+    assert open_with(pre, None, "no_suffix_file") == kmc.KMC_EIO
+    assert open_with(b"KMCX" + pre[4:], suf, "bad_marker") == kmc.KMC_EIO
+    assert open_with(pre[:-4] + b"KMCX", suf, "bad_end_marker") == kmc.KMC_EIO
+    assert open_with(pre, suf[:-5] + b"KMCS", "truncated_records") == kmc.KMC_EIO
+    bad_pos = pre[:-8] + (70).to_bytes(4, "little") + b"KMCP"
+    assert open_with(bad_pos, suf, "bad_header_position") == kmc.KMC_EIO
+    assert db.value is None
+    assert lib.kmc_db_open(None, b"x", 0) == kmc.KMC_EINVAL
+    assert "kmc_pre" in kmc.strerror(kmc.KMC_EIO) or "kmc_suf" in kmc.strerror(kmc.KMC_EIO)
