@@ -441,6 +441,12 @@ int kmc_count_small_noalloc(const char *d_bases, const uint64_t *d_offsets, uint
 /* Computes signatures with the tile-doubling scan kernel instead of the
  * lane-block one (both give the same super k-mers; for cross-checks). */
 #define KMC_DEBUG_SIG_TILE 8u
+/* Bins by canonical minimizers (the smallest canonical m-mer, no Sect. 2.2
+ * filter) instead of signatures: the comparison of Sect. 2.2 and of the
+ * paper's signatures-versus-minimizers table (super k-mers per read, k-mers
+ * in the largest bin).  The counts are the same; kmc_db_write refuses such a
+ * handle (KMC_EINVAL), the format's map being one of signatures. */
+#define KMC_DEBUG_MINIMIZER 16u
 
 #ifdef __cplusplus
 }

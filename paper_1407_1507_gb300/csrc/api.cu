@@ -210,7 +210,7 @@ int validate(const kmc_params *p) {
   if (p->canonical != 1) return KMC_EINVAL;
   if (p->reserved0 || p->reserved[0]) return KMC_EINVAL;
   if (p->debug_flags & ~(KMC_DEBUG_KEEP_SUPERKMERS | KMC_DEBUG_KEEP_KEYS | KMC_DEBUG_NARROW_SORT |
-                         KMC_DEBUG_SIG_TILE))
+                         KMC_DEBUG_SIG_TILE | KMC_DEBUG_MINIMIZER))
     return KMC_EINVAL;
   return KMC_OK;
 }

@@ -144,6 +144,7 @@ struct SigArgs {
   const uint64_t *set_starts;      // stream position where set s begins, [n_slots + 1]
   uint32_t n_slots;                // 0 or 1: a single set
   uint32_t bins_per_slot;
+  uint32_t no_filter;              // 1: canonical minimizers (no Sect. 2.2 filter)
 };
 
 // Set holding stream position pos (largest s with set_starts[s] <= pos).
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(SIG_THREADS) sig_kernel(SigArgs a) {
       uint32_t f = (uint32_t)get_bits(s.pk, (uint64_t)(2 * (pos - LB)), 2 * m);
       uint32_t r = revcomp32(f, m);
       uint32_t c = f < r ? f : r;            // canonical m-mer (Sect. 2.1)
-      v = mmer_allowed(c, m) ? c : SENT;     // Sect. 2.2 filter
+      v = (a.no_filter || mmer_allowed(c, m)) ? c : SENT;  // Sect. 2.2 filter
     }
     s.mm[0][j] = v;
   }
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
       fw = ((fw << 2) | c) & mmask;
       rc = (rc >> 2) | ((3u - c) << rsh);
       const uint32_t cn = fw < rc ? fw : rc;                 // canonical m-mer (Sect. 2.1)
-      const uint32_t v = mmer_allowed(cn, m) ? cn : SENT;     // Sect. 2.2 filter
+      const uint32_t v = (a.no_filter || mmer_allowed(cn, m)) ? cn : SENT;  // Sect. 2.2 filter
       V[L * stride + j] = (VT)v;
       pm = v < pm ? v : pm;
       P[L * stride + j] = (VT)pm;

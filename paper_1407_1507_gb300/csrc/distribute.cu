@@ -59,6 +59,7 @@ int stage_stream(Handle &h, const char *piece_ptr, const uint64_t *d_offsets, ui
 SigArgs sig_args(Handle &h, const StreamInfo &si, const uint64_t *d_offsets, uint64_t n_reads,
                  uint64_t byte_start) {
   SigArgs a{};
+  a.no_filter = (h.p.debug_flags & KMC_DEBUG_MINIMIZER) ? 1u : 0u;
   a.packed = as<uint64_t>(h.ds.packed);
   a.inval = as<uint64_t>(h.ds.inval);
   a.smask = as<uint64_t>(h.ds.starts);
@@ -217,6 +218,7 @@ int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_
   for (uint32_t b = 0; b < B; ++b) {
     h.bin_kmers[b] += hk[b];
     pc->n_kmers += hk[b];
+    if (h.bin_kmers[b] > h.stats.max_bin_kmers) h.stats.max_bin_kmers = h.bin_kmers[b];
   }
   if (dev_ensure(pc->index, (n_rec + 1) * 8, h.st) ||
       dev_ensure(pc->words, (n_words + STREAM_PAD_WORDS) * 8, h.st) ||

@@ -31,6 +31,7 @@ KMC_DEBUG_KEEP_SUPERKMERS = 1
 KMC_DEBUG_KEEP_KEYS = 2
 KMC_DEBUG_NARROW_SORT = 4
 KMC_DEBUG_SIG_TILE = 8
+KMC_DEBUG_MINIMIZER = 16
 
 
 class kmc_params(ctypes.Structure):

@@ -120,3 +120,12 @@ def test_db_mid_workload_scaled(tmp_path):
     pre, suf = DB.write(w.k, w.m, vals, [int(x) for x in cnt], [int(x) for x in mp], w.n_bins, 2, 10 ** 9)
     assert open(base + ".kmc_pre", "rb").read() == pre
     assert open(base + ".kmc_suf", "rb").read() == suf
+
+
+def test_db_write_refuses_minimizer_bins(tmp_path):
+    b, o = oracle.as_reads(["ACGTACGGTCATTGCAACGTACGGTCATTGCA"] * 3)
+    with kmc.Counter(12, m=5, n_bins=4, debug_flags=kmc.KMC_DEBUG_MINIMIZER) as c:
+        c.add(b, o).count()
+        with pytest.raises(kmc.KmcError) as e:
+            c.write_db(str(tmp_path / "x"))
+        assert e.value.code == kmc.KMC_EINVAL

@@ -212,11 +212,14 @@ def test_device_input_equals_host_input():
 
 
 @pytest.mark.parametrize("k,m,flags", [(28, 7, 0), (28, 7, 8), (21, 9, 0), (64, 7, 0), (64, 7, 8),
-                                        (12, 7, 0), (40, 11, 0), (32, 5, 0)])
+                                        (12, 7, 0), (40, 11, 0), (32, 5, 0), (28, 7, 16), (28, 7, 24),
+                                        (55, 5, 16), (12, 7, 16)])
 def test_superkmers_match_oracle_split(k, m, flags):
     # flags 8 = KMC_DEBUG_SIG_TILE (tile-doubling signature kernel); k=12, m=7
-    # (window of 6 m-mers) takes that kernel in any case
+    # (window of 6 m-mers) takes that kernel in any case; 16 =
+    # KMC_DEBUG_MINIMIZER (canonical minimizers, no Sect. 2.2 filter)
     w = synth.mid(scale=0.0005)
+    use_minimizer = bool(flags & kmc.KMC_DEBUG_MINIMIZER)
     flags |= kmc.KMC_DEBUG_KEEP_SUPERKMERS
     with kmc.Counter(k, m=m, n_bins=64, debug_flags=flags) as c:
         c.add(w.bases, w.offsets)
@@ -225,9 +228,16 @@ def test_superkmers_match_oracle_split(k, m, flags):
     want = []
     for r in range(w.n_reads):
         a, e = int(w.offsets[r]), int(w.offsets[r + 1])
-        for st, n, g in oracle.superkmers(bytes(w.bases[a:e]), k, m, cut_every=128):
+        for st, n, g in oracle.superkmers(bytes(w.bases[a:e]), k, m, use_minimizer=use_minimizer, cut_every=128):
             want.append((r, st, n, g))
     assert got == sorted(want)
+
+
+@pytest.mark.parametrize("k,m", [(28, 7), (55, 9), (21, 5)])
+def test_minimizer_bins_keep_the_counts(k, m):
+    w = synth.mid(scale=0.002)
+    got = gpu_count(w.bases, w.offsets, k, m=m, n_bins=512, debug_flags=kmc.KMC_DEBUG_MINIMIZER)
+    assert_same(got, oracle_count(w.bases, w.offsets, k))
 
 
 def test_bin_map_matches_oracle_reading():
@@ -236,10 +246,15 @@ def test_bin_map_matches_oracle_reading():
     with kmc.Counter(k, m=m, n_bins=B) as c:
         c.add(w.bases, w.offsets)
         got = kmc.kmc_get_bin_map(c.h, 4 ** m + 1)
+        largest = c.stats()["max_bin_kmers"]
     ps = oracle.position_sigs(w.bases, w.offsets, k, m)
     ps = ps[ps != oracle.NO_KMER]
     weights = np.bincount(ps, minlength=4 ** m + 1).astype(np.uint64)
-    assert np.array_equal(got, oracle.bin_map(weights, B))
+    want = oracle.bin_map(weights, B)
+    assert np.array_equal(got, want)
+    # the largest bin's k-mer positions (the statistic of the paper's
+    # signatures-versus-minimizers table)
+    assert largest == int(np.bincount(want[ps], minlength=B).max())
 
 
 def test_user_bin_map_does_not_change_result():
