@@ -188,3 +188,35 @@ def batch_set(i: int, scale: float = 1.0) -> Workload:
     g = genome_markov3(max(_scaled(genome, scale, 1000), L), seed)
     b, o = reads(g, np.full(_scaled(n_reads, scale), L), 0.01, 0.0, seed + 1)
     return Workload(f"batch{i}", b, o, k=k, m=7, n_bins=64)
+
+
+# ------------------------------------------------------------- file formats
+
+def to_fastq(bases: np.ndarray, offsets: np.ndarray, seed: int = BASE_SEED, crlf: bool = False) -> bytes:
+    """The reads as a FASTQ file: "@r<i>" headers, "+" lines, and seeded
+    quality strings drawn from '!'..'J' (they contain letters that are also
+    bases)."""
+    rng = np.random.default_rng(seed)
+    nl = b"\r\n" if crlf else b"\n"
+    parts = []
+    off = np.asarray(offsets, dtype=np.int64)
+    raw = np.asarray(bases, dtype=np.uint8)
+    for i in range(off.size - 1):
+        a, e = int(off[i]), int(off[i + 1])
+        q = (rng.integers(33, 75, e - a)).astype(np.uint8).tobytes()
+        parts += [b"@r%d" % i, nl, raw[a:e].tobytes(), nl, b"+", nl, q, nl]
+    return b"".join(parts)
+
+
+def to_fasta(bases: np.ndarray, offsets: np.ndarray, width: int = 60) -> bytes:
+    """The reads as a multi-FASTA file: ">s<i>" headers, sequences wrapped at
+    `width` bases per line."""
+    parts = []
+    off = np.asarray(offsets, dtype=np.int64)
+    raw = np.asarray(bases, dtype=np.uint8)
+    for i in range(off.size - 1):
+        a, e = int(off[i]), int(off[i + 1])
+        parts += [b">s%d\n" % i]
+        for j in range(a, e, width):
+            parts += [raw[j:min(e, j + width)].tobytes(), b"\n"]
+    return b"".join(parts)
