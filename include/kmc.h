@@ -167,6 +167,26 @@ int kmc_add_reads(kmc_handle *h, const char *bases, const uint64_t *offsets, uin
 int kmc_add_reads_device(kmc_handle *h, const char *d_bases, const uint64_t *d_offsets,
                          uint64_t n_reads, uint64_t n_bases);
 
+/* FASTQ or FASTA file contents (Sect. 2.4: reads come from FASTQ/FASTA
+ * files; Suppl. S1 -fq, -fa, -fm), read on the device; the host only copies
+ * the bytes.  format KMC_FORMAT_FASTQ: records of four lines ("@" header,
+ * sequence, "+" line, quality); each sequence line is a read.
+ * KMC_FORMAT_FASTA (also multi-FASTA): records of a ">" header line and any
+ * number of sequence lines; a record's read is its sequence lines joined
+ * without line breaks (a genome may be one read).  In both, a "\r" that ends
+ * a line is dropped, a final newline may be missing, and the read's bytes
+ * follow the conventions of kmc_add_reads (any byte other than A/C/G/T breaks
+ * it).  n_reads and n_bases of kmc_stats count the reads and their bases.
+ * kmc_add_file_bytes takes host memory (copied before it returns),
+ * kmc_add_file_bytes_device device memory (read during the call).  Errors:
+ * KMC_EINVAL (unknown format), KMC_EINPUT (a FASTQ record that does not
+ * start with "@", has no "+" line or is incomplete; a FASTA file that does
+ * not start with ">"), KMC_ESTATE, KMC_ENOMEM, KMC_ECUDA. */
+#define KMC_FORMAT_FASTQ 1u
+#define KMC_FORMAT_FASTA 2u
+int kmc_add_file_bytes(kmc_handle *h, const char *bytes, uint64_t n_bytes, uint32_t format);
+int kmc_add_file_bytes_device(kmc_handle *h, const char *d_bytes, uint64_t n_bytes, uint32_t format);
+
 /* Runs the sorting phase over all reads added and keeps the result on the
  * device.  Blocks until done.  May be called again (it recounts the same
  * reads).  Errors: KMC_ESTATE (no kmc_add_reads since open/reset is fine:

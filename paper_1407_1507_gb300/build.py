@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmc.so")
 SOURCES = ["api.cu", "distribute.cu", "count.cu", "order.cu", "scan.cu", "noalloc.cu", "batch.cu", "server.cu",
-           "db.cu"]
+           "db.cu", "parse.cu"]
 HEADERS = ["common.cuh", "sortlib.cuh", "internal.h", "dist_kernels.cuh", "kx_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -174,7 +174,9 @@ void release_all(Handle &h) {
                     &h.ss.sorted_keys, &h.ss.big_list, &h.ss.big_scratch, &h.ss.sv_keys,
                     &h.ss.sv_counts, &h.ss.acc_keys, &h.ss.acc_counts, &h.ss.counters, &h.ss.o_hist, &h.ss.o_base, &h.ss.o_cursor,
                     &h.ss.o_flags, &h.ss.o_flag_scan, &h.ss.o_tile_first, &h.ss.o_scan_tmp,
-                    &h.ss.o_big_list, &h.ss.o_big_k, &h.ss.o_big_v};
+                    &h.ss.o_big_list, &h.ss.o_big_k, &h.ss.o_big_v, &h.ds.fq_raw, &h.ds.fq_cnt,
+                    &h.ds.fq_base, &h.ds.fq_tmp, &h.ds.fq_small, &h.ds.fq_hdr, &h.ds.fq_bases,
+                    &h.ds.fq_offsets};
   for (DevBuf *b : bufs) dev_release(*b, h.st);
   for (int i = 0; i < 2; ++i) {
     if (h.ds.stage_host[i]) cudaFreeHost(h.ds.stage_host[i]);
@@ -473,6 +475,58 @@ int kmc_add_reads_device(kmc_handle *kh, const char *d_bases, const uint64_t *d_
   h.stats.n_reads += n_reads;
   h.stats.n_bases += n_bases;
   return KMC_OK;
+}
+
+// FASTQ / FASTA bytes in device memory: parsed on the device into reads,
+// then distributed like kmc_add_reads_device.
+static int add_file_device(Handle &h, const char *d_bytes, uint64_t n_bytes, uint32_t format) {
+  const char *d_bases = nullptr;
+  const uint64_t *d_offsets = nullptr;
+  uint64_t n_reads = 0, n_bases = 0;
+  KMC_CUDA_TRY(cudaEventRecord(h.ev[0], h.st));
+  int rc = parse_reads(h, reinterpret_cast<const uint8_t *>(d_bytes), n_bytes, format == KMC_FORMAT_FASTQ,
+                       &d_bases, &d_offsets, &n_reads, &n_bases);
+  if (rc) return rc;
+  if (n_reads == 0) return KMC_OK;
+  rc = add_device(h, d_bases, d_offsets, n_reads, n_bases, h.stats.n_reads);
+  if (rc) return rc;
+  KMC_CUDA_TRY(cudaEventRecord(h.ev[1], h.st));
+  rc = check_device_error(h);
+  if (rc) return rc;
+  h.timer.resolve();
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h.ev[0], h.ev[1]);
+  h.stats.ms_distribute += ms;
+  h.stats.n_reads += n_reads;
+  h.stats.n_bases += n_bases;
+  return KMC_OK;
+}
+
+int kmc_add_file_bytes_device(kmc_handle *kh, const char *d_bytes, uint64_t n_bytes, uint32_t format) {
+  if (!kh) return KMC_EINVAL;
+  Handle &h = kh->h;
+  if (h.counted) return KMC_ESTATE;
+  if (format != KMC_FORMAT_FASTQ && format != KMC_FORMAT_FASTA) return KMC_EINVAL;
+  if (n_bytes == 0) return KMC_OK;
+  if (!d_bytes) return KMC_EINVAL;
+  DeviceGuard g(h.p.device);
+  LaunchScope ls(h);
+  return add_file_device(h, d_bytes, n_bytes, format);
+}
+
+int kmc_add_file_bytes(kmc_handle *kh, const char *bytes, uint64_t n_bytes, uint32_t format) {
+  if (!kh) return KMC_EINVAL;
+  Handle &h = kh->h;
+  if (h.counted) return KMC_ESTATE;
+  if (format != KMC_FORMAT_FASTQ && format != KMC_FORMAT_FASTA) return KMC_EINVAL;
+  if (n_bytes == 0) return KMC_OK;
+  if (!bytes) return KMC_EINVAL;
+  DeviceGuard g(h.p.device);
+  LaunchScope ls(h);
+  // the raw file goes to the device as it is; nothing is parsed on the host
+  if (dev_ensure(h.ds.fq_raw, n_bytes + 64, h.st)) return KMC_ENOMEM;
+  KMC_CUDA_TRY(cudaMemcpyAsync(h.ds.fq_raw.p, bytes, n_bytes, cudaMemcpyHostToDevice, h.st));
+  return add_file_device(h, static_cast<const char *>(h.ds.fq_raw.p), n_bytes, format);
 }
 
 int kmc_add_reads(kmc_handle *kh, const char *bases, const uint64_t *offsets, uint64_t n_reads) {

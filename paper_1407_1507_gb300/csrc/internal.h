@@ -74,6 +74,9 @@ struct DistScratch {
   // the piece being distributed
   cudaStream_t copy_st = nullptr;
   cudaEvent_t copy_done[2] = {nullptr, nullptr}, buf_free[2] = {nullptr, nullptr}, go = nullptr;
+  // FASTQ / FASTA input: the raw file (host input), per-chunk counts and
+  // their scans, header flags per line, the reads' bases and offsets
+  DevBuf fq_raw, fq_cnt, fq_base, fq_tmp, fq_small, fq_hdr, fq_bases, fq_offsets;
 };
 
 // Per-call scratch of the sorting phase.
@@ -158,6 +161,10 @@ struct LaunchScope {
   explicit LaunchScope(Handle &hh) : h(hh), l0(g_launches) {}
   ~LaunchScope() { h.timer.launches += g_launches - l0; }
 };
+
+// parse.cu: FASTQ / FASTA bytes in device memory -> reads (handle scratch)
+int parse_reads(Handle &h, const uint8_t *d_raw, uint64_t n, bool fastq, const char **d_bases,
+                const uint64_t **d_offsets, uint64_t *n_reads, uint64_t *n_bases);
 
 // distribute.cu
 int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_offsets,

@@ -32,6 +32,8 @@ KMC_DEBUG_KEEP_KEYS = 2
 KMC_DEBUG_NARROW_SORT = 4
 KMC_DEBUG_SIG_TILE = 8
 KMC_DEBUG_MINIMIZER = 16
+KMC_FORMAT_FASTQ = 1
+KMC_FORMAT_FASTA = 2
 
 
 class kmc_params(ctypes.Structure):
@@ -137,6 +139,8 @@ SIGNATURES = [
     ("kmc_open", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(kmc_params)]),
     ("kmc_add_reads", ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_uint64]),
     ("kmc_add_reads_device", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint64]),
+    ("kmc_add_file_bytes", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint32]),
+    ("kmc_add_file_bytes_device", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint32]),
     ("kmc_count", ctypes.c_int, [_vp]),
     ("kmc_result_size", ctypes.c_int, [_vp, _u64p]),
     ("kmc_result", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_uint64, _u64p]),
@@ -240,6 +244,19 @@ def kmc_add_reads_ptr(h, bases_ptr: int, offsets_ptr: int, n_reads: int):
 def kmc_add_reads_device(h, d_bases_ptr: int, d_offsets_ptr: int, n_reads: int, n_bases: int):
     _check(load().kmc_add_reads_device(h, d_bases_ptr, d_offsets_ptr, n_reads, n_bases),
            "kmc_add_reads_device")
+
+
+def kmc_add_file_bytes(h, data, fmt: int):
+    """FASTQ (KMC_FORMAT_FASTQ) or FASTA (KMC_FORMAT_FASTA) file contents in
+    host memory (bytes or a uint8 array); parsed on the device."""
+    buf = np.frombuffer(data, dtype=np.uint8) if isinstance(data, (bytes, bytearray)) else \
+        np.ascontiguousarray(data, dtype=np.uint8)
+    _check(load().kmc_add_file_bytes(h, buf.ctypes.data if buf.size else None, buf.size, fmt),
+           "kmc_add_file_bytes")
+
+
+def kmc_add_file_bytes_device(h, d_bytes_ptr: int, n_bytes: int, fmt: int):
+    _check(load().kmc_add_file_bytes_device(h, d_bytes_ptr, n_bytes, fmt), "kmc_add_file_bytes_device")
 
 
 def kmc_count(h):
@@ -489,6 +506,14 @@ class Counter:
 
     def add(self, bases, offsets):
         kmc_add_reads(self.h, bases, offsets)
+        return self
+
+    def add_file(self, data, fmt):
+        """FASTQ / FASTA file contents (host bytes, or a torch CUDA uint8 tensor)."""
+        if hasattr(data, "data_ptr"):
+            kmc_add_file_bytes_device(self.h, data.data_ptr(), data.numel(), fmt)
+        else:
+            kmc_add_file_bytes(self.h, data, fmt)
         return self
 
     def add_device(self, d_bases, d_offsets):
