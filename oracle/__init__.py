@@ -72,6 +72,10 @@ def _load():
                                      ctypes.c_uint64, ctypes.c_int, ctypes.c_int, u64p, u32p,
                                      ctypes.c_uint64, u64p, u64p]
         lib.oracle_count.restype = ctypes.c_int
+        lib.oracle_count_mode.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                          ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p,
+                                          u32p, ctypes.c_uint64, u64p, u64p]
+        lib.oracle_count_mode.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -90,8 +94,12 @@ def as_reads(reads):
 
 
 def count(bases, offsets, k, cutoff_min=1, cutoff_max=2**32 - 1, threads=1, passes=1,
-          return_npos=False):
-    """Plain-definition count (C).  Returns (kmers uint64[n, words], counts uint32[n])."""
+          return_npos=False, canonical=True, counter_max=0):
+    """Plain-definition count (C).  Returns (kmers uint64[n, words], counts uint32[n]).
+
+    canonical=False counts k-mers as read (Suppl. S1 -b).  counter_max > 0
+    reports min(count, counter_max) for the k-mers the cutoffs keep (Suppl. S1
+    -cs, "maximal value of a counter"; the cutoffs apply to the true count)."""
     lib = _load()
     bases = np.ascontiguousarray(bases, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
@@ -102,10 +110,10 @@ def count(bases, offsets, k, cutoff_min=1, cutoff_max=2**32 - 1, threads=1, pass
     kms = np.zeros((1, words), dtype=np.uint64)
     cnt = np.zeros(1, dtype=np.uint32)
     for _ in range(2):
-        rc = lib.oracle_count(_p(bases, ctypes.c_uint8), _p(offsets, ctypes.c_uint64),
-                              offsets.size - 1, k, cutoff_min, cutoff_max, threads, passes,
-                              _p(kms, ctypes.c_uint64), _p(cnt, ctypes.c_uint32), cap,
-                              ctypes.byref(n_out), ctypes.byref(n_pos))
+        rc = lib.oracle_count_mode(_p(bases, ctypes.c_uint8), _p(offsets, ctypes.c_uint64),
+                                   offsets.size - 1, k, cutoff_min, cutoff_max, int(bool(canonical)),
+                                   threads, passes, _p(kms, ctypes.c_uint64), _p(cnt, ctypes.c_uint32),
+                                   cap, ctypes.byref(n_out), ctypes.byref(n_pos))
         if rc == -3:
             cap = n_out.value
             kms = np.zeros((max(cap, 1), words), dtype=np.uint64)
@@ -115,7 +123,10 @@ def count(bases, offsets, k, cutoff_min=1, cutoff_max=2**32 - 1, threads=1, pass
             raise RuntimeError(f"oracle_count failed: {rc}")
         break
     n = n_out.value
-    res = (kms[:n], cnt[:n])
+    cnt = cnt[:n]
+    if counter_max:
+        cnt = np.minimum(cnt, np.uint32(min(counter_max, 2**32 - 1)))
+    res = (kms[:n], cnt)
     return res + (n_pos.value,) if return_npos else res
 
 

@@ -370,6 +370,7 @@ typedef struct {
   uint64_t n_out, out_cap;
   uint64_t n_pos; /* valid k-mer positions seen (all partitions) */
   int err;
+  int canonical;  /* 1: canonical k-mers (Sect. 2.1); 0: as read (Suppl. S1 -b) */
 } work_t;
 
 static void *count_worker(void *arg) {
@@ -392,7 +393,7 @@ static void *count_worker(void *arg) {
       if (!window_valid(codes, p, k)) continue;
       u128 f = value_of(codes + p, k);
       u128 rc = revcomp_value_of(codes + p, k);
-      u128 c = f < rc ? f : rc; /* canonical k-mer */
+      u128 c = (w->canonical && rc < f) ? rc : f; /* canonical k-mer, or as read */
       w->n_pos++;
       if (hash128(c) % w->n_parts != w->part) continue;
       if (table_add(&t, c)) { w->err = -1; goto done; }
@@ -431,9 +432,24 @@ static int cmp_kc(const void *a, const void *b) {
  * `cap` is too small (n_out is still set).  n_pos_out (if not NULL) receives
  * the number of valid k-mer positions.
  */
+int oracle_count_mode(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads, int k,
+                      uint64_t ci, uint64_t cx, int canonical, int n_threads, int n_passes,
+                      uint64_t *out_words, uint32_t *out_counts, uint64_t cap, uint64_t *n_out,
+                      uint64_t *n_pos_out);
+
 int oracle_count(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads, int k,
                  uint64_t ci, uint64_t cx, int n_threads, int n_passes, uint64_t *out_words,
                  uint32_t *out_counts, uint64_t cap, uint64_t *n_out, uint64_t *n_pos_out) {
+  return oracle_count_mode(bases, offsets, n_reads, k, ci, cx, 1, n_threads, n_passes, out_words,
+                           out_counts, cap, n_out, n_pos_out);
+}
+
+/* As oracle_count; canonical = 0 counts the k-mers as they are read
+ * (Suppl. S1 option -b: no transformation into canonical form). */
+int oracle_count_mode(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads, int k,
+                      uint64_t ci, uint64_t cx, int canonical, int n_threads, int n_passes,
+                      uint64_t *out_words, uint32_t *out_counts, uint64_t cap, uint64_t *n_out,
+                      uint64_t *n_pos_out) {
   if (k < 1 || k > 64 || n_threads < 1 || n_passes < 1) return -1;
   uint64_t total = 0, npos = 0;
   int rc = 0;
@@ -448,6 +464,7 @@ int oracle_count(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads
       w[t].k = k;
       w[t].ci = ci;
       w[t].cx = cx;
+      w[t].canonical = canonical;
       w[t].part = (uint64_t)q * (uint64_t)n_threads + (uint64_t)t;
       w[t].n_parts = (uint64_t)n_passes * (uint64_t)n_threads;
       if (n_threads > 1) pthread_create(&th[t], NULL, count_worker, &w[t]);

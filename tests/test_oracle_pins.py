@@ -372,3 +372,39 @@ def test_bin_map_properties():
     # uniform weights: equal group sizes
     mp2 = oracle.bin_map(np.ones(1024, np.uint64), 16)
     assert np.array_equal(np.bincount(mp2, minlength=16), np.full(16, 64))
+
+
+# ----------------------------------------------- -b and -cs (Suppl. S1 options)
+
+@pytest.mark.parametrize("seed", range(6))
+def test_noncanonical_count_is_the_forward_kmers(seed):
+    rng = random.Random(500 + seed)
+    k = rng.choice([1, 3, 8, 21, 32, 33, 50])
+    reads = ["".join(rng.choice("ACGTN") for _ in range(rng.randint(0, 120))) for _ in range(40)]
+    b, o = oracle.as_reads(reads)
+    kms, cnt = oracle.count(b, o, k, 1, canonical=False)
+    got = dict(zip(oracle.kmers_to_int(kms), cnt.tolist()))
+    from collections import Counter
+    want = Counter(S.value(s) for r in reads for s in S.kmers(r, k))
+    assert got == dict(want)
+    # the canonical count of c is the forward count of c plus that of its
+    # reverse complement (once for a palindrome)
+    ck, cc = oracle.count(b, o, k, 1)
+    for v, n in zip(oracle.kmers_to_int(ck), cc.tolist()):
+        s = S.from_value(v, k)
+        r = S.value(S.revcomp(s))
+        assert n == got.get(v, 0) + (got.get(r, 0) if r != v else 0)
+
+
+def test_counter_max_saturates_after_the_cutoffs():
+    reads = ["ACGT" * 30, "TTTTTTTTTTTT", "ACGTACGTAC"]
+    b, o = oracle.as_reads(reads)
+    full_k, full_c = oracle.count(b, o, 4, 1)
+    sat_k, sat_c = oracle.count(b, o, 4, 1, counter_max=5)
+    assert np.array_equal(full_k, sat_k) and np.array_equal(sat_c, np.minimum(full_c, 5))
+    assert full_c.max() > 5
+    # the cutoffs look at the true count: cx = 10 drops k-mers seen more often
+    # even though their reported count would be 5
+    cut_k, cut_c = oracle.count(b, o, 4, 1, cutoff_max=10, counter_max=5)
+    keep = full_c <= 10
+    assert np.array_equal(cut_k, full_k[keep]) and np.array_equal(cut_c, np.minimum(full_c[keep], 5))
