@@ -67,7 +67,9 @@ typedef struct {
   uint32_t x;          /* (k,x)-mer extension, 0..3, or KMC_AUTO (Sect. 2.3)      */
   uint64_t cutoff_min; /* keep count >= cutoff_min (Suppl. S1 -ci; default 2)     */
   uint64_t cutoff_max; /* keep count <= cutoff_max (Suppl. S1 -cx; default 1e9)   */
-  uint32_t canonical;  /* must be 1: canonical k-mers (Sect. 2.1)                 */
+  uint32_t canonical;  /* 1: canonical k-mers (Sect. 2.1, default); 0: k-mers as
+                          read, no transformation into canonical form (Suppl.
+                          S1 -b), with x = 0 or KMC_AUTO only                 */
   int32_t device;      /* CUDA device ordinal                                     */
   void *cuda_stream;   /* cudaStream_t to run on, or NULL for a stream of the
                           handle's own                                        */
@@ -86,7 +88,10 @@ typedef struct {
                           most a quarter each; a single bin larger than a
                           wave is still sorted whole.  Never changes the
                           result.  Not applied to x > 0.                      */
-  uint64_t reserved[1];/* must be zero                                            */
+  uint64_t counter_max;/* 0: exact counts (default); else a count above it is
+                          reported as counter_max (Suppl. S1 -cs, "maximal
+                          value of a counter"); the cutoffs apply to the true
+                          count.  kmc_count only (batched / served: 0)         */
 } kmc_params;
 
 /* Fills *p with the paper's defaults: k=25, m=7, 512 bins, x=KMC_AUTO,
@@ -261,7 +266,8 @@ int kmc_get_bin_map(const kmc_handle *h, uint32_t *map, uint64_t n_entries);
  * records and prefix arrays are built on the device (each k-mer's
  * signature, Sect. 2.2, picks its bin through the map).  path is the common
  * prefix of the two file names.  Errors: KMC_ESTATE (before kmc_count),
- * KMC_EIO (a file cannot be written), KMC_ENOMEM, KMC_ECUDA.
+ * KMC_EINVAL (a handle counting k-mers as read, canonical = 0, or binning
+ * by minimizers), KMC_EIO (a file cannot be written), KMC_ENOMEM, KMC_ECUDA.
  *
  * kmc_db_open: reads a database with the format section's procedure (both
  * markers, the header position, the header, the map and prefix arrays, the

@@ -209,8 +209,9 @@ int validate(const kmc_params *p) {
   if (p->n_bins < 1 || p->n_bins > 65536) return KMC_EINVAL;
   if (p->x != KMC_AUTO && p->x > 3) return KMC_EINVAL;
   if (p->cutoff_min > p->cutoff_max) return KMC_EINVAL;
-  if (p->canonical != 1) return KMC_EINVAL;
-  if (p->reserved0 || p->reserved[0]) return KMC_EINVAL;
+  if (p->canonical > 1) return KMC_EINVAL;
+  if (!p->canonical && p->x != 0 && p->x != KMC_AUTO) return KMC_EINVAL;  // (k,x)-mers are canonical
+  if (p->reserved0) return KMC_EINVAL;
   if (p->debug_flags & ~(KMC_DEBUG_KEEP_SUPERKMERS | KMC_DEBUG_KEEP_KEYS | KMC_DEBUG_NARROW_SORT |
                          KMC_DEBUG_SIG_TILE | KMC_DEBUG_MINIMIZER))
     return KMC_EINVAL;

@@ -692,7 +692,8 @@ int kmc_batch_open(kmc_batch **out, const kmc_params *p, uint64_t max_bases, uin
   *out = nullptr;
   if (max_bases < 1024 || max_reads < 1 || max_sets < 1 || max_sets > (1u << 16)) return KMC_EINVAL;
   if (max_bases > (1ull << 31)) return KMC_EINVAL;
-  if (p->cutoff_min > p->cutoff_max || p->canonical != 1 || p->m < 1 || p->m > KMC_MAX_M) return KMC_EINVAL;
+  if (p->cutoff_min > p->cutoff_max || p->canonical != 1 || p->counter_max || p->m < 1 || p->m > KMC_MAX_M)
+    return KMC_EINVAL;
   if (flags & ~(KMC_BATCH_AUTOTUNE | KMC_BATCH_NO_GRAPH)) return KMC_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) {

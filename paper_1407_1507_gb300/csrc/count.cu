@@ -457,6 +457,7 @@ int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_
   if (rc) return rc;
   KxArgs<K> a;
   a.n_chunks_dyn = nullptr;
+  a.noncanonical = h.p.canonical ? 0 : 1;
   a.chunks = meta.chunks;
   a.pieces = meta.pieces;
   a.k = k;
@@ -854,7 +855,8 @@ uint32_t resolve_x(uint32_t k, uint32_t x) {
   return x;
 }
 
-int sort_phase(Handle &h) {
+namespace {
+int sort_phase_any(Handle &h) {
   const uint32_t k = h.p.k;
   const int x = (int)resolve_x(k, h.p.x);
   h.stats.n_waves = 1;
@@ -868,6 +870,23 @@ int sort_phase(Handle &h) {
     return sort_phase_kx<u128, uint64_t>(h, x);
   }
   return sort_phase_kx<u128, u128>(h, x);
+}
+
+// Suppl. S1 -cs: counts above the counter's maximal value are reported as it.
+__global__ void saturate_kernel(uint32_t *__restrict__ c, uint64_t n, uint32_t cmax) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    if (c[i] > cmax) c[i] = cmax;
+}
+}  // namespace
+
+int sort_phase(Handle &h) {
+  const int rc = sort_phase_any(h);
+  if (rc || !h.p.counter_max || !h.n_out) return rc;
+  const uint32_t cmax = (uint32_t)std::min<uint64_t>(h.p.counter_max, 0xFFFFFFFFull);
+  saturate_kernel<<<grid_for(h.n_out, 256, 65535), 256, 0, h.st>>>(as<uint32_t>(h.out_counts), h.n_out, cmax);
+  KMC_COUNT_LAUNCH();
+  KMC_CUDA_TRY(cudaGetLastError());
+  return KMC_OK;
 }
 
 namespace {

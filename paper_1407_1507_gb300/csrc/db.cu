@@ -295,6 +295,7 @@ int kmc_db_write(kmc_handle *kh, const char *path) {
   Handle &h = kh->h;
   if (!h.counted || !h.map_ready) return KMC_ESTATE;
   if (h.p.debug_flags & KMC_DEBUG_MINIMIZER) return KMC_EINVAL;  // the format's map is by signature
+  if (!h.p.canonical) return KMC_EINVAL;  // lookups take the canonical form
   DeviceGuard g(h.p.device);
   const int k = (int)h.p.k, m = (int)h.m_used;
   const uint32_t B = h.p.n_bins;

@@ -104,7 +104,14 @@ struct KxArgs {
   const uint8_t *group_D;      // digit bits of each bin
   Mixer<K> mixer;
   const unsigned long long *n_chunks_dyn;  // batches: chunk count on the device (else NULL)
+  int noncanonical = 0;                    // 1: keys are the k-mers as read (Suppl. S1 -b)
 };
+
+// The key of k-mer j of a record: canonical (Sect. 2.1), or as read (-b).
+template <typename K>
+__device__ __forceinline__ K kmer_key(const KxArgs<K> &a, const uint64_t *wds, uint32_t j) {
+  return a.noncanonical ? get_kmer<K>(wds, j, a.k) : canonical_kmer<K>(wds, j, a.k);
+}
 
 constexpr int KX_SMEM_D = 12;            // digits aggregated in shared memory up to 2^12
 constexpr int KX_STASH = 1024;           // keys stashed per warp between the two sweeps
@@ -125,7 +132,7 @@ __device__ __forceinline__ void for_chunk_keys(const KxArgs<K> &a, const Chunk &
       const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
       const bool ok = 32 * it + lane < b.total;
       K key = K(0);
-      if (ok) key = a.mixer.mix(canonical_kmer<K>(pd.words + woff, j, a.k));
+      if (ok) key = a.mixer.mix(kmer_key<K>(a, pd.words + woff, j));
       f(ok, key);
     }
   }
@@ -224,7 +231,7 @@ kx0_scatter_kernel(KxArgs<K> a, const uint64_t *__restrict__ bucket_base,
         uint32_t rec, j;
         locate(b, it, &rec, &j);
         const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
-        key = ok ? a.mixer.mix(canonical_kmer<K>(pd.words + woff, j, a.k)) : K(0);
+        key = ok ? a.mixer.mix(kmer_key<K>(a, pd.words + woff, j)) : K(0);
       }
       const uint32_t d = ok ? top_digit<K>(key, a.key_bits, D) : 0xFFFFFFFFu;
       uint64_t p = 0;
@@ -341,7 +348,7 @@ kx0_gen_kernel(KxArgs<K> a, const uint32_t *__restrict__ sgroup_base, uint32_t *
       locate(b, it, &rec, &j);
       const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
       if (32 * it + lane >= b.total) continue;
-      const K key = a.mixer.mix(canonical_kmer<K>(pd.words + woff, j, a.k));
+      const K key = a.mixer.mix(kmer_key<K>(a, pd.words + woff, j));
       const uint64_t p = kb + 32 * it + lane;
       if (p < n_keys) keys[p] = key; else atomicOr(err, ERR_CAPACITY);
       atomicAdd(&s.h[upper_digit<K>(key, a.key_bits, D)], 1u);

@@ -43,7 +43,7 @@ class kmc_params(ctypes.Structure):
         ("canonical", ctypes.c_uint32), ("device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
         ("debug_flags", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
         ("piece_bytes", ctypes.c_uint64), ("device_budget", ctypes.c_uint64),
-        ("reserved", ctypes.c_uint64 * 1),
+        ("counter_max", ctypes.c_uint64),
     ]
 
 
@@ -483,7 +483,8 @@ def kmc_server_close(s):
 # ----------------------------------------------------------- convenience
 
 def make_params(k, m=7, n_bins=512, x=KMC_AUTO, cutoff_min=2, cutoff_max=10**9, device=0,
-                stream=None, debug_flags=0, piece_bytes=0, device_budget=0) -> kmc_params:
+                stream=None, debug_flags=0, piece_bytes=0, device_budget=0, canonical=1,
+                counter_max=0) -> kmc_params:
     p = kmc_default_params()
     p.k, p.m, p.n_bins = k, m, n_bins
     p.x = KMC_AUTO if x is None else x
@@ -493,6 +494,8 @@ def make_params(k, m=7, n_bins=512, x=KMC_AUTO, cutoff_min=2, cutoff_max=10**9, 
     p.debug_flags = debug_flags
     p.piece_bytes = piece_bytes
     p.device_budget = device_budget
+    p.canonical = canonical
+    p.counter_max = counter_max
     return p
 
 

@@ -62,7 +62,7 @@ def test_strerror_names_every_code(lib):
 
 
 @pytest.mark.parametrize("field,value", [("k", 0), ("k", 65), ("m", 0), ("m", 12), ("n_bins", 0),
-                                         ("n_bins", 65537), ("x", 4), ("canonical", 0),
+                                         ("n_bins", 65537), ("x", 4), ("canonical", 2),
                                          ("reserved0", 1), ("debug_flags", 32)])
 def test_open_rejects_bad_params_on_host(lib, field, value):
     p = kmc.kmc_default_params()
@@ -70,6 +70,14 @@ def test_open_rejects_bad_params_on_host(lib, field, value):
     h = ctypes.c_void_p()
     assert lib.kmc_open(ctypes.byref(h), ctypes.byref(p)) == kmc.KMC_EINVAL
     assert h.value is None
+
+
+def test_open_rejects_noncanonical_kx_mers(lib):
+    # k-mers as read (Suppl. S1 -b) are counted with x = 0 only
+    p = kmc.kmc_default_params()
+    p.canonical, p.x = 0, 2
+    h = ctypes.c_void_p()
+    assert lib.kmc_open(ctypes.byref(h), ctypes.byref(p)) == kmc.KMC_EINVAL
 
 
 def test_open_rejects_inverted_cutoffs(lib):

@@ -129,3 +129,12 @@ def test_db_write_refuses_minimizer_bins(tmp_path):
         with pytest.raises(kmc.KmcError) as e:
             c.write_db(str(tmp_path / "x"))
         assert e.value.code == kmc.KMC_EINVAL
+
+
+def test_db_write_refuses_noncanonical_counts(tmp_path):
+    b, o = oracle.as_reads(["ACGTACGGTCATTGCAACGTACGGTCATTGCA"] * 3)
+    with kmc.Counter(12, m=5, n_bins=4, canonical=0) as c:
+        c.add(b, o).count()
+        with pytest.raises(kmc.KmcError) as e:
+            c.write_db(str(tmp_path / "x"))
+        assert e.value.code == kmc.KMC_EINVAL

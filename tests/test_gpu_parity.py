@@ -374,3 +374,25 @@ def test_kx_keys_per_bin_match_oracle_split(k, x):
                 want[int(mp[g])].append(_kx_key(v, xp, k, x))
     for b in range(B):
         assert got[b] == sorted(want[b]), f"bin {b}"
+
+
+@pytest.mark.parametrize("k", [1, 5, 21, 28, 32, 55, 64])
+def test_noncanonical_counts(k):
+    # Suppl. S1 -b: k-mers as read, no canonical form
+    w = synth.mid(scale=0.002)
+    got = gpu_count(w.bases, w.offsets, k, m=w.m, n_bins=w.n_bins, canonical=0)
+    want = oracle.count(w.bases, w.offsets, k, 2, 10 ** 9, threads=8, canonical=False)
+    assert want[0].shape[0] > 0
+    assert_same(got, want)
+
+
+@pytest.mark.parametrize("k,cmax,x", [(28, 40, kmc.KMC_AUTO), (28, 255, 0), (31, 3, 0), (55, 10, 0), (25, 7, 2),
+                                      (21, 1, 3)])
+def test_counter_max_saturates(k, cmax, x):
+    # Suppl. S1 -cs: counts above the counter's maximal value are reported as it
+    w = synth.mid(scale=0.002)
+    got = gpu_count(w.bases, w.offsets, k, m=w.m, n_bins=w.n_bins, x=x, counter_max=cmax)
+    want = oracle.count(w.bases, w.offsets, k, 2, 10 ** 9, threads=8, counter_max=cmax)
+    exact = oracle.count(w.bases, w.offsets, k, 2, 10 ** 9, threads=8)
+    assert int(want[1].max()) == min(cmax, int(exact[1].max()))
+    assert_same(got, want)
