@@ -477,9 +477,14 @@ int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_
     K *gen_keys = as<K>(ss.keys_gen);
     {
       StageScope sc(h, KMC_STAGE_KX_COUNT);
-      kx0_gen_kernel<K><<<(unsigned)meta.n_chunks, KX_THREADS, 0, h.st>>>(
-          a, meta.sgroup_base, meta.super_hist, meta.bin_key_base, meta.bin_fill, gen_keys, n_keys,
-          as<uint32_t>(h.err));
+      if (a.noncanonical)
+        kx0_gen_kernel<K, true><<<(unsigned)meta.n_chunks, KX_THREADS, 0, h.st>>>(
+            a, meta.sgroup_base, meta.super_hist, meta.bin_key_base, meta.bin_fill, gen_keys, n_keys,
+            as<uint32_t>(h.err));
+      else
+        kx0_gen_kernel<K, false><<<(unsigned)meta.n_chunks, KX_THREADS, 0, h.st>>>(
+            a, meta.sgroup_base, meta.super_hist, meta.bin_key_base, meta.bin_fill, gen_keys, n_keys,
+            as<uint32_t>(h.err));
       KMC_COUNT_LAUNCH();
       KMC_CUDA_TRY(cudaGetLastError());
     }

@@ -413,7 +413,10 @@ inline size_t sig2_smem_bytes(int k, int m, uint32_t n_bins) {
 // The lane-block form pays off once a block holds several positions.
 inline bool sig2_applies(int k, int m) { return k - m + 1 >= 8 && k - m + 1 <= SIG2_MAXW; }
 
-template <typename VT>
+// VT: 16- or 32-bit m-mer values; NOFILTER: canonical minimizers instead of
+// signatures (a compile-time switch, so that the signature scan pays
+// nothing for it).
+template <typename VT, bool NOFILTER>
 __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = threadIdx.x;
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
       fw = ((fw << 2) | c) & mmask;
       rc = (rc >> 2) | ((3u - c) << rsh);
       const uint32_t cn = fw < rc ? fw : rc;                 // canonical m-mer (Sect. 2.1)
-      const uint32_t v = (a.no_filter || mmer_allowed(cn, m)) ? cn : SENT;  // Sect. 2.2 filter
+      const uint32_t v = (NOFILTER || mmer_allowed(cn, m)) ? cn : SENT;  // Sect. 2.2 filter
       V[L * stride + j] = (VT)v;
       pm = v < pm ? v : pm;
       P[L * stride + j] = (VT)pm;
@@ -694,12 +697,13 @@ inline cudaError_t sig_prepare() {
   if (dev < 64 && done[dev].load()) return cudaSuccess;
   e = cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SigSmem));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sig2_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sig2_smem_bytes(SIG2_MAXW, 8, SIG_SMEM_BINS));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sig2_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sig2_smem_bytes(SIG2_MAXW, 1, SIG_SMEM_BINS));
-  if (e != cudaSuccess) return e;
+  const int s32 = (int)sig2_smem_bytes(SIG2_MAXW, 8, SIG_SMEM_BINS);
+  const int s16 = (int)sig2_smem_bytes(SIG2_MAXW, 1, SIG_SMEM_BINS);
+  if ((e = cudaFuncSetAttribute(sig2_kernel<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32)) ||
+      (e = cudaFuncSetAttribute(sig2_kernel<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32)) ||
+      (e = cudaFuncSetAttribute(sig2_kernel<uint16_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s16)) ||
+      (e = cudaFuncSetAttribute(sig2_kernel<uint16_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s16)))
+    return e;
   if (dev < 64) done[dev].store(1);
   return cudaSuccess;
 }
@@ -712,10 +716,14 @@ inline int sig_launch(const SigArgs &a, uint64_t n_stream, bool tile, cudaStream
     const uint64_t own = (uint64_t)sig2_own(a.k, a.m);
     const uint64_t g = (n_stream + own - 1) / own;
     if (g == 0) return 0;
-    if (a.m <= 7)
-      sig2_kernel<uint16_t><<<(unsigned)g, SIG2_LANES, sig2_smem_bytes(a.k, a.m, a.n_bins), st>>>(a);
-    else
-      sig2_kernel<uint32_t><<<(unsigned)g, SIG2_LANES, sig2_smem_bytes(a.k, a.m, a.n_bins), st>>>(a);
+    const size_t sm = sig2_smem_bytes(a.k, a.m, a.n_bins);
+    if (a.m <= 7) {
+      if (a.no_filter) sig2_kernel<uint16_t, true><<<(unsigned)g, SIG2_LANES, sm, st>>>(a);
+      else sig2_kernel<uint16_t, false><<<(unsigned)g, SIG2_LANES, sm, st>>>(a);
+    } else {
+      if (a.no_filter) sig2_kernel<uint32_t, true><<<(unsigned)g, SIG2_LANES, sm, st>>>(a);
+      else sig2_kernel<uint32_t, false><<<(unsigned)g, SIG2_LANES, sm, st>>>(a);
+    }
     return 1;
   }
   const uint64_t g = (n_stream + SIG_TPOS - 1) / SIG_TPOS;

@@ -10,7 +10,7 @@ namespace kmc {
 namespace {
 
 constexpr int KX_THREADS = 256;
-constexpr int KX_RECORDS_PER_CHUNK = 1024;
+constexpr int KX_RECORDS_PER_CHUNK = 2048;
 constexpr int CNT_THREADS = 256;
 constexpr int CNT_IPT64 = 16;   // tile = 4096 64-bit keys
 constexpr int CNT_IPT128 = 8;   // tile = 2048 128-bit keys
@@ -308,7 +308,7 @@ __device__ __forceinline__ uint32_t lower_digit(K key, int key_bits, int D) {
 }
 
 // sgroup_base[bin]: index of the bin's first super bucket (2^S per bin).
-template <typename K>
+template <typename K, bool NONCANON = false>
 __global__ void __launch_bounds__(KX_THREADS)
 kx0_gen_kernel(KxArgs<K> a, const uint32_t *__restrict__ sgroup_base, uint32_t *__restrict__ super_hist,
                const uint64_t *__restrict__ bin_key_base, unsigned long long *__restrict__ bin_fill,
@@ -348,7 +348,8 @@ kx0_gen_kernel(KxArgs<K> a, const uint32_t *__restrict__ sgroup_base, uint32_t *
       locate(b, it, &rec, &j);
       const uint64_t woff = __shfl_sync(FULL, b.woff, rec);
       if (32 * it + lane >= b.total) continue;
-      const K key = a.mixer.mix(kmer_key<K>(a, pd.words + woff, j));
+      const K key = a.mixer.mix(NONCANON ? get_kmer<K>(pd.words + woff, j, a.k)
+                                         : canonical_kmer<K>(pd.words + woff, j, a.k));
       const uint64_t p = kb + 32 * it + lane;
       if (p < n_keys) keys[p] = key; else atomicOr(err, ERR_CAPACITY);
       atomicAdd(&s.h[upper_digit<K>(key, a.key_bits, D)], 1u);
