@@ -27,7 +27,7 @@
  *                         histogram of a sample (our reading of the merge
  *                         heuristic, see oracle_bin_map).
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open (all listed with the design notes):
  *   - any byte other than upper-case A, C, G, T breaks a read; no k-mer
  *     spans it or a read boundary;
  *   - both count cutoffs are inclusive for kept k-mers (ci <= n <= cx);
