@@ -217,16 +217,20 @@ int db_build(Handle &h, int lut, std::vector<uint64_t> &firsts, std::vector<uint
   const int k = (int)h.p.k, m = (int)h.m_used, words = h.key_words;
   const uint32_t B = h.p.n_bins;
   const uint64_t NP = (uint64_t)B << (2 * lut);
-  DevBuf keys, idx, cnt, fst, tmp, mx, rec;
-  auto release = [&]() {
-    for (DevBuf *b : {&keys, &idx, &cnt, &fst, &tmp, &mx, &rec}) dev_release(*b, h.st);
-  };
+  // scratch of this call, released (stream-ordered) on every return path
+  struct Scratch {
+    DevBuf keys, idx, cnt, fst, tmp, mx, rec;
+    cudaStream_t st;
+    ~Scratch() {
+      for (DevBuf *b : {&keys, &idx, &cnt, &fst, &tmp, &mx, &rec}) dev_release(*b, st);
+    }
+  } sc;
+  sc.st = h.st;
+  DevBuf &keys = sc.keys, &idx = sc.idx, &cnt = sc.cnt, &fst = sc.fst, &tmp = sc.tmp, &mx = sc.mx, &rec = sc.rec;
   if (dev_ensure(keys, (n + 1) * 8, h.st) || dev_ensure(idx, (n + 1) * 4, h.st) ||
       dev_ensure(cnt, NP * 4 + 4, h.st) || dev_ensure(fst, (NP + 1) * 8, h.st) ||
-      dev_ensure(tmp, scan_tmp_words(NP) * 8, h.st) || dev_ensure(mx, 8, h.st)) {
-    release();
+      dev_ensure(tmp, scan_tmp_words(NP) * 8, h.st) || dev_ensure(mx, 8, h.st))
     return KMC_ENOMEM;
-  }
   KMC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, NP * 4, h.st));
   KMC_CUDA_TRY(cudaMemsetAsync(mx.p, 0, 4, h.st));
   if (n) {
@@ -240,25 +244,16 @@ int db_build(Handle &h, int lut, std::vector<uint64_t> &firsts, std::vector<uint
   uint32_t maxc = 0;
   KMC_CUDA_TRY(cudaMemcpyAsync(&maxc, mx.p, 4, cudaMemcpyDeviceToHost, h.st));
   int rc = check_device_error(h);  // synchronises
-  if (rc) {
-    release();
-    return rc;
-  }
+  if (rc) return rc;
   const int csize = db_counter_size(maxc);
   const int rb = (k - lut) / 4 + csize;
   if (n > 1) {
     int bb = 1;
     while (bb < 32 && (1ull << bb) < B) ++bb;
     rc = sort_pairs_u64(h, as<uint64_t>(keys), as<uint32_t>(idx), n, 32 + bb);
-    if (rc) {
-      release();
-      return rc;
-    }
+    if (rc) return rc;
   }
-  if (dev_ensure(rec, n * rb + 16, h.st)) {
-    release();
-    return KMC_ENOMEM;
-  }
+  if (dev_ensure(rec, n * rb + 16, h.st)) return KMC_ENOMEM;
   if (n) {
     db_record_kernel<K><<<db_grid(n), DB_THREADS, 0, h.st>>>(as<uint64_t>(h.out_kmers), as<uint32_t>(h.out_counts),
                                                              as<uint32_t>(idx), n, words, k, lut, csize,
@@ -271,7 +266,6 @@ int db_build(Handle &h, int lut, std::vector<uint64_t> &firsts, std::vector<uint
   KMC_CUDA_TRY(cudaMemcpyAsync(firsts.data(), fst.p, (NP + 1) * 8, cudaMemcpyDeviceToHost, h.st));
   if (n) KMC_CUDA_TRY(cudaMemcpyAsync(records.data(), rec.p, n * rb, cudaMemcpyDeviceToHost, h.st));
   KMC_CUDA_TRY(cudaStreamSynchronize(h.st));
-  release();
   *csize_out = csize;
   return KMC_OK;
 }
