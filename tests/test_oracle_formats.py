@@ -45,3 +45,18 @@ def test_fasta_must_start_with_a_header():
         F.parse_fasta(b"ACGT\n>x\nAC\n")
     with pytest.raises(ValueError):
         F.parse_fasta(b"\n>x\nAC\n")
+
+
+def test_generator_files_read_back_as_the_reads():
+    # the seeded FASTQ / FASTA writers used by the GPU tests produce files that
+    # the readers turn back into exactly the generator's reads
+    import oracle
+    from paper_1407_1507_gb300 import synth
+    w = synth.tiny(scale=0.002)
+    reads = [bytes(w.bases[w.offsets[i]:w.offsets[i + 1]]).decode() for i in range(w.n_reads)]
+    assert F.parse_fastq(synth.to_fastq(w.bases, w.offsets)) == reads
+    assert F.parse_fastq(synth.to_fastq(w.bases, w.offsets, crlf=True)) == reads
+    for width in (1, 7, 60, 1000):
+        assert F.parse_fasta(synth.to_fasta(w.bases, w.offsets, width=width)) == reads
+    b, o = oracle.as_reads(reads)
+    assert bytes(b) == bytes(w.bases) and list(o) == list(w.offsets)
