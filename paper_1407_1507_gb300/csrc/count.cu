@@ -74,15 +74,15 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
   constexpr int GIPT = TILE / GRP_THREADS;
   using GSM = TileGroupSmem<K, GRP_THREADS, GIPT>;
   const bool grouped = !sorted_out && out.sort_bits == kCountSortBits;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceOnce attr;
+  if (!attr.done()) {
     KMC_CUDA_TRY(cudaFuncSetAttribute(tile_count_kernel<K, CNT_THREADS, IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(tile_group_kernel<K, GRP_THREADS, GIPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GSM)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(big_count_kernel<K, CNT_THREADS, BIG_IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BSM)));
-    attr = true;
+    attr.set();
   }
   int occ = 0;
   // 64-bit keys below 2^62 are counted through a hash table per tile
@@ -90,11 +90,11 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
   using HSM = TileHashSmem<HTHREADS, HIPT>;
   const bool hashed = grouped && sizeof(K) == 8 && plan.key_bits <= 62;
   if constexpr (sizeof(K) == 8) if (hashed) {
-    static bool hattr = false;
-    if (!hattr) {
+    static DeviceOnce hattr;
+    if (!hattr.done()) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(tile_hash_kernel<HTHREADS, HIPT>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HSM)));
-      hattr = true;
+      hattr.set();
     }
     if (dev_ensure(ss.tile_desc, ((size_t)plan.NB + 1) * sizeof(TileDesc), h.st)) return KMC_ENOMEM;
     TilePlan gplan = plan;
@@ -148,11 +148,11 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
       if (dev_ensure(ss.big_scratch, (n_keys + 2) * sizeof(K), h.st)) return KMC_ENOMEM;
       scratch = as<K>(ss.big_scratch);
     }
-    static bool battr = false;
-    if (!battr) {
+    static DeviceOnce battr;
+    if (!battr.done()) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(big_group_kernel<K, GRP_THREADS, GIPT, GIPT>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BGS)));
-      battr = true;
+      battr.set();
     }
     StageScope sc(h, KMC_STAGE_BIG_SORT);
     big_group_kernel<K, GRP_THREADS, GIPT, GIPT><<<std::min<uint32_t>(nbig, (uint32_t)h.sm_count), GRP_THREADS,
@@ -505,13 +505,13 @@ int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_
     sa.n_units = (uint32_t)meta.n_units;
     sa.n_super = meta.n_super;
     sa.err = as<uint32_t>(h.err);
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (!attr.done()) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_sweep_kernel<K, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(SweepSmem<K>)));
       KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_sweep_kernel<K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(SweepSmem<K>)));
-      attr = true;
+      attr.set();
     }
     StageScope sc(h, KMC_STAGE_KX_SCATTER);
     // upper digits: generated keys -> super buckets (in ss.keys)
@@ -544,11 +544,11 @@ int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_
   if (rc) return rc;
   if (meta.n_chunks && !meta.gen) {
     KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, NB * 4, h.st));  // hist becomes the per-bucket cursor
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (!attr.done()) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)sizeof(KxScatterSmem<K>)));
-      attr = true;
+      attr.set();
     }
     StageScope sc(h, KMC_STAGE_KX_SCATTER);
     kx0_scatter_kernel<K><<<(unsigned)meta.n_chunks, KX_THREADS, sizeof(KxScatterSmem<K>), h.st>>>(
@@ -799,13 +799,13 @@ int sort_phase_kx(Handle &h, int x) {
   out.sort_bits = (h.p.debug_flags & KMC_DEBUG_NARROW_SORT) ? 8 : kCountSortBits;
   out.slots = nullptr;
   out.bins_per_slot = 1;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceOnce attr;
+  if (!attr.done()) {
     KMC_CUDA_TRY(cudaFuncSetAttribute(tile_wcount_kernel<K0, CNT_THREADS, IPT2>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WSM)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(big_wcount_kernel<K0, CNT_THREADS, BIG_IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BWSM)));
-    attr = true;
+    attr.set();
   }
   int occ = 0;
   KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(

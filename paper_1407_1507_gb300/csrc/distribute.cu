@@ -235,11 +235,11 @@ int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_
   KMC_CUDA_TRY(cudaMemcpyAsync(h_rec, rec_base, (size_t)B * 8, cudaMemcpyDeviceToDevice, h.st));
   KMC_CUDA_TRY(cudaMemcpyAsync(h_words, word_base, (size_t)B * 8, cudaMemcpyDeviceToDevice, h.st));
   if (n_rec) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static DeviceOnce attr_set;
+    if (!attr_set.done()) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)scat_smem_bytes(SIG_SMEM_BINS)));
-      attr_set = true;
+      attr_set.set();
     }
     StageScope sc(h, KMC_STAGE_BIN_SCATTER);
     scatter_kernel<<<(unsigned)((n_rec + SCAT_PER_CTA - 1) / SCAT_PER_CTA), SCAT_THREADS,

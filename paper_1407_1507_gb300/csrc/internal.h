@@ -1,5 +1,6 @@
 // Host-side internals shared by the translation units of libkmc.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -11,6 +12,25 @@ namespace kmc {
 
 int cuda_fail(cudaError_t e, const char *what);
 void set_error_text(const char *msg);  // the text kmc_strerror gives for KMC_EIO
+
+// "Done once" per CUDA device: kernel attributes (shared-memory limits) are
+// per device, so a process that uses several devices sets them on each.
+struct DeviceOnce {
+  std::atomic<uint64_t> mask{0};
+  static int dev() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+  }
+  bool done() const {
+    const int d = dev();
+    return d < 64 && ((mask.load() >> d) & 1ull);
+  }
+  void set() {
+    const int d = dev();
+    if (d < 64) mask.fetch_or(1ull << d);
+  }
+};
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {

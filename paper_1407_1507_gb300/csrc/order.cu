@@ -117,13 +117,13 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
   plan.n_groups = 1;
   plan.NB = ND;
   plan.key_bits = key_bits;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceOnce attr;
+  if (!attr.done()) {
     KMC_CUDA_TRY(cudaFuncSetAttribute(tile_pairs_kernel<K, V, PAIR_THREADS, PAIR_IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(big_pairs_kernel<K, V, PAIR_THREADS, PAIR_BIG_IPT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BSM)));
-    attr = true;
+    attr.set();
   }
   auto *c32 = as<uint32_t>(ss.o_cursor);
   auto *c64 = reinterpret_cast<unsigned long long *>(c32 + 4);  // c64[0..1] = bytes 16..31
