@@ -92,6 +92,13 @@ def test_null_handles_are_rejected(lib):
     assert lib.kmc_count(None) == kmc.KMC_EINVAL
     assert lib.kmc_result_size(None, ctypes.byref(n)) == kmc.KMC_EINVAL
     lib.kmc_close(None)  # no-op
+    assert lib.kmc_add_file_bytes(None, b"@a\nA\n+\nI\n", 8, kmc.KMC_FORMAT_FASTQ) == kmc.KMC_EINVAL
+    assert lib.kmc_add_file_bytes_device(None, None, 8, kmc.KMC_FORMAT_FASTA) == kmc.KMC_EINVAL
+    assert lib.kmc_db_write(None, b"x") == kmc.KMC_EINVAL
+    info = kmc.kmc_db_info()
+    assert lib.kmc_db_info_get(None, ctypes.byref(info)) == kmc.KMC_EINVAL
+    assert lib.kmc_db_lookup(None, None, 1, None, None) == kmc.KMC_EINVAL
+    lib.kmc_db_close(None)  # no-op
 
 
 def test_db_open_rejects_missing_and_malformed_files(lib, tmp_path):
