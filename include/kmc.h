@@ -11,6 +11,12 @@
  * of this library: 2-bit packing, the signature scan (Sect. 2.2), super
  * k-mer binning (Sect. 2.4, Fig. 1), (k,x)-mer construction (Sect. 2.3),
  * radix sorting, expansion and run-length counting (Sect. 2.4, Fig. 2).
+ * Options of Suppl. S1 beyond these: k-mers as read instead of canonical
+ * (-b, kmc_params.canonical = 0) and a counter maximum (-cs,
+ * kmc_params.counter_max).  Around the counting path: FASTQ / FASTA input
+ * read on the device (kmc_add_file_bytes), KMC 2's database files with
+ * batched lookups (kmc_db_*), batched read sets (kmc_batch_*) and a
+ * request server (kmc_server_*).
  *
  * Conventions (all calls):
  *   - Return KMC_OK (0) on success, a negative KMC_E* code otherwise;
@@ -47,7 +53,7 @@ extern "C" {
 #define KMC_ETRUNC (-6)    /* caller capacity too small; *n_out still set    */
 #define KMC_ETIMEOUT (-7)  /* a device-side bounded wait gave up            */
 #define KMC_EAGAIN (-8)    /* not ready yet (server poll)                   */
-#define KMC_EINPUT (-9)    /* malformed read offsets                         */
+#define KMC_EINPUT (-9)    /* malformed read offsets or FASTQ / FASTA file    */
 #define KMC_EIO (-10)      /* a database file cannot be read or written, or
                               is not in the KMC 2 format                    */
 
