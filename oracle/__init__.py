@@ -76,6 +76,12 @@ def _load():
                                           ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p,
                                           u32p, ctypes.c_uint64, u64p, u64p]
         lib.oracle_count_mode.restype = ctypes.c_int
+        lib.oracle_count_sample.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, u64p, u32p, ctypes.c_uint64, u64p, u64p]
+        lib.oracle_count_sample.restype = ctypes.c_int
+        lib.oracle_hash_parts.argtypes = [u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, u64p]
+        lib.oracle_hash_parts.restype = None
         _lib = lib
     return _lib
 
@@ -128,6 +134,46 @@ def count(bases, offsets, k, cutoff_min=1, cutoff_max=2**32 - 1, threads=1, pass
         cnt = np.minimum(cnt, np.uint32(min(counter_max, 2**32 - 1)))
     res = (kms[:n], cnt)
     return res + (n_pos.value,) if return_npos else res
+
+
+def count_sample(bases, offsets, k, cutoff_min, cutoff_max, passes, which, threads=16):
+    """Exact counts of one hash class of k-mers (about 1/passes of them) and
+    the number of valid k-mer positions: (kmers, counts, n_pos).  The class
+    is the k-mers c with in_sample(c) true for the same (passes, which,
+    threads)."""
+    lib = _load()
+    bases = np.ascontiguousarray(bases, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    words = (k + 31) // 32
+    n_out, n_pos = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    cap = 0
+    kms = np.zeros((1, words), dtype=np.uint64)
+    cnt = np.zeros(1, dtype=np.uint32)
+    for _ in range(2):
+        rc = lib.oracle_count_sample(_p(bases, ctypes.c_uint8), _p(offsets, ctypes.c_uint64), offsets.size - 1,
+                                     k, cutoff_min, cutoff_max, 1, threads, passes, which,
+                                     _p(kms, ctypes.c_uint64), _p(cnt, ctypes.c_uint32), cap,
+                                     ctypes.byref(n_out), ctypes.byref(n_pos))
+        if rc == -3:
+            cap = n_out.value
+            kms = np.zeros((max(cap, 1), words), dtype=np.uint64)
+            cnt = np.zeros(max(cap, 1), dtype=np.uint32)
+            continue
+        if rc != 0:
+            raise RuntimeError(f"oracle_count_sample failed: {rc}")
+        break
+    n = n_out.value
+    return kms[:n], cnt[:n], n_pos.value
+
+
+def in_sample(kmers, k, passes, which, threads=16):
+    """Boolean mask: which of the k-mers (uint64[n, words]) count_sample keeps."""
+    kms = np.ascontiguousarray(kmers, dtype=np.uint64)
+    h = np.empty(kms.shape[0], dtype=np.uint64)
+    if kms.shape[0]:
+        _load().oracle_hash_parts(_p(kms, ctypes.c_uint64), kms.shape[0], k, passes * threads,
+                                  _p(h, ctypes.c_uint64))
+    return (h // np.uint64(threads)) == np.uint64(which)
 
 
 def position_sigs(bases, offsets, k, m):

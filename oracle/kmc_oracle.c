@@ -444,17 +444,53 @@ int oracle_count(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads
                            out_counts, cap, n_out, n_pos_out);
 }
 
+static int count_passes(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads, int k,
+                        uint64_t ci, uint64_t cx, int canonical, int n_threads, int n_passes,
+                        int q_first, int q_last, uint64_t *out_words, uint32_t *out_counts,
+                        uint64_t cap, uint64_t *n_out, uint64_t *n_pos_out);
+
 /* As oracle_count; canonical = 0 counts the k-mers as they are read
  * (Suppl. S1 option -b: no transformation into canonical form). */
 int oracle_count_mode(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads, int k,
                       uint64_t ci, uint64_t cx, int canonical, int n_threads, int n_passes,
                       uint64_t *out_words, uint32_t *out_counts, uint64_t cap, uint64_t *n_out,
                       uint64_t *n_pos_out) {
+  return count_passes(bases, offsets, n_reads, k, ci, cx, canonical, n_threads, n_passes, 0, n_passes,
+                      out_words, out_counts, cap, n_out, n_pos_out);
+}
+
+/* One pass of oracle_count_mode with n_passes passes: the exact counts of the
+ * k-mers c with (hash(c) mod (n_passes * n_threads)) div n_threads == which,
+ * about 1/n_passes of them (a sample of a result too large to hold). */
+int oracle_count_sample(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads, int k,
+                        uint64_t ci, uint64_t cx, int canonical, int n_threads, int n_passes, int which,
+                        uint64_t *out_words, uint32_t *out_counts, uint64_t cap, uint64_t *n_out,
+                        uint64_t *n_pos_out) {
+  if (which < 0 || which >= n_passes) return -1;
+  return count_passes(bases, offsets, n_reads, k, ci, cx, canonical, n_threads, n_passes, which, which + 1,
+                      out_words, out_counts, cap, n_out, n_pos_out);
+}
+
+/* hash(c) mod n_parts of n k-mer values (ceil(k/32) words each, most
+ * significant first), the class oracle_count_sample selects by. */
+void oracle_hash_parts(const uint64_t *words, uint64_t n, int k, uint64_t n_parts, uint64_t *out) {
+  const int w = (k + 31) / 32;
+  for (uint64_t i = 0; i < n; ++i) {
+    u128 v = 0;
+    for (int j = 0; j < w; ++j) v = (v << 64) | words[i * w + j];
+    out[i] = hash128(v) % n_parts;
+  }
+}
+
+static int count_passes(const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads, int k,
+                        uint64_t ci, uint64_t cx, int canonical, int n_threads, int n_passes,
+                        int q_first, int q_last, uint64_t *out_words, uint32_t *out_counts,
+                        uint64_t cap, uint64_t *n_out, uint64_t *n_pos_out) {
   if (k < 1 || k > 64 || n_threads < 1 || n_passes < 1) return -1;
   uint64_t total = 0, npos = 0;
   int rc = 0;
   const int words = (k + 31) / 32;
-  for (int q = 0; q < n_passes && rc == 0; ++q) {
+  for (int q = q_first; q < q_last && rc == 0; ++q) {
     work_t *w = (work_t *)calloc((size_t)n_threads, sizeof(work_t));
     pthread_t *th = (pthread_t *)malloc((size_t)n_threads * sizeof(pthread_t));
     for (int t = 0; t < n_threads; ++t) {
@@ -477,7 +513,7 @@ int oracle_count_mode(const uint8_t *bases, const uint64_t *offsets, uint64_t n_
       if (w[t].err) rc = -1;
       pass_n += w[t].n_out;
     }
-    if (q == 0) npos = w[0].n_pos;
+    if (q == q_first) npos = w[0].n_pos;
     kc_t *all = (kc_t *)malloc((pass_n ? pass_n : 1) * sizeof(kc_t));
     uint64_t j = 0;
     for (int t = 0; t < n_threads; ++t) {
@@ -503,7 +539,7 @@ int oracle_count_mode(const uint8_t *bases, const uint64_t *offsets, uint64_t n_
   *n_out = total;
   if (n_pos_out) *n_pos_out = npos;
   if (rc) return rc;
-  if (n_passes > 1 && total <= cap) {
+  if (q_last - q_first > 1 && total <= cap) {
     /* merge the per-pass sorted runs: one more plain sort over the words */
     kc_t *all = (kc_t *)malloc((total ? total : 1) * sizeof(kc_t));
     for (uint64_t i = 0; i < total; ++i) {

@@ -408,3 +408,19 @@ def test_counter_max_saturates_after_the_cutoffs():
     cut_k, cut_c = oracle.count(b, o, 4, 1, cutoff_max=10, counter_max=5)
     keep = full_c <= 10
     assert np.array_equal(cut_k, full_k[keep]) and np.array_equal(cut_c, np.minimum(full_c[keep], 5))
+
+
+def test_sampled_count_is_a_hash_class_of_the_full_count():
+    # the sample oracle (one pass of the hash-partitioned count) equals the
+    # full count restricted to its class; the classes partition the k-mers
+    from paper_1407_1507_gb300 import synth
+    w = synth.mid(scale=0.001)
+    for k in (28, 55):
+        fk, fc, npos = oracle.count(w.bases, w.offsets, k, 2, 10 ** 9, threads=4, return_npos=True)
+        seen = np.zeros(fk.shape[0], dtype=np.int64)
+        for which in range(4):
+            sk, sc, spos = oracle.count_sample(w.bases, w.offsets, k, 2, 10 ** 9, 4, which, threads=3)
+            m = oracle.in_sample(fk, k, 4, which, threads=3)
+            assert np.array_equal(fk[m], sk) and np.array_equal(fc[m], sc) and spos == npos
+            seen += m
+        assert np.all(seen == 1)
