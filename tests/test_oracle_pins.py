@@ -424,3 +424,18 @@ def test_sampled_count_is_a_hash_class_of_the_full_count():
             assert np.array_equal(fk[m], sk) and np.array_equal(fc[m], sc) and spos == npos
             seen += m
         assert np.all(seen == 1)
+
+
+@pytest.mark.parametrize("k,prefix", [(28, "ACCTG"), (21, "TT"), (32, "ACGTA"), (5, "C"), (28, "AAAAAAAA"),
+                                      (31, "GATTACA")])
+def test_prefix_class_counts_match_the_full_count(k, prefix):
+    # the numpy prefix-class counter (used on the full-size workload) against
+    # the C oracle's complete count and valid-position total
+    from oracle import windows as WN
+    from paper_1407_1507_gb300 import synth
+    w = synth.mid(scale=0.001)
+    fk, fc, npos = oracle.count(w.bases, w.offsets, k, 1, threads=4, return_npos=True)
+    v, n, np_ = WN.prefix_class_counts(w.bases, w.offsets, k, prefix, chunk_reads=7_000)
+    m = (fk[:, 0] >> np.uint64(2 * (k - len(prefix)))) == np.uint64(S.value(prefix))
+    assert np_ == npos
+    assert np.array_equal(v, fk[m, 0]) and np.array_equal(n, fc[m].astype(np.int64))
