@@ -326,6 +326,7 @@ def run_ours(args, rank, local_rank, world):
                    "scale": args.scale, "n_bins": B},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "stages": stages,
         "cpu_baseline": cpu, "clocks": clk, "modes": modes,
+        "bases_per_s": job_rate(int(w.bases.size), world, ms),
     }
     return out
 
