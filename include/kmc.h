@@ -56,6 +56,7 @@ extern "C" {
 #define KMC_EINPUT (-9)    /* malformed read offsets or FASTQ / FASTA file    */
 #define KMC_EIO (-10)      /* a database file cannot be read or written, or
                               is not in the KMC 2 format                    */
+#define KMC_ECANCELED (-11) /* the job was cancelled (kmc_server_cancel)    */
 
 #define KMC_AUTO 0xFFFFFFFFu
 #define KMC_MAX_K 64u
@@ -424,6 +425,12 @@ int kmc_server_wait(kmc_server *s, uint64_t job_id, double timeout_s);
 int kmc_server_result(kmc_server *s, uint64_t job_id, const uint64_t **kmers,
                       const uint32_t **counts, uint64_t *n, double *latency_ms);
 int kmc_server_release(kmc_server *s, uint64_t job_id);
+/* kmc_server_cancel: a job still waiting in the queue is removed from it and
+ *   ends with KMC_ECANCELED (kmc_server_wait and kmc_server_result return
+ *   it; release it as any other finished job).  A job already admitted to a
+ *   batch runs to the end: KMC_ESTATE, and so for a finished job.
+ *   Errors: KMC_EINVAL (unknown job). */
+int kmc_server_cancel(kmc_server *s, uint64_t job_id);
 int kmc_server_stats_get(kmc_server *s, kmc_server_stats *st);
 void kmc_server_close(kmc_server *s);
 
@@ -479,6 +486,20 @@ int kmc_count_small_noalloc(const char *d_bases, const uint64_t *d_offsets, uint
  * in the largest bin).  The counts are the same; kmc_db_write refuses such a
  * handle (KMC_EINVAL), the format's map being one of signatures. */
 #define KMC_DEBUG_MINIMIZER 16u
+/* Failure-path check of the device-side bounded waits: the tile kernel of
+ * wide keys (k >= 32, x = 0) first waits, with a limit of 200 us, on an
+ * mbarrier that nothing arrives on; the wait gives up, the kernel waits
+ * (bounded) for its own bulk copy still in flight, reports the timeout and
+ * returns, and kmc_count returns KMC_ETIMEOUT.  The handle must then be
+ * closed; the CUDA context stays usable. */
+#define KMC_DEBUG_WAIT_TIMEOUT 32u
+
+/* Failure-path check of the host side: after `after` more successful device
+ * or pinned host allocations of this library (any handle, any thread), the
+ * next one fails as if the memory were exhausted, once; the call that made
+ * it returns KMC_ENOMEM and the handle can still be closed.  after < 0
+ * cancels a pending injection.  For tests only. */
+int kmc_debug_fail_alloc(int64_t after);
 
 #ifdef __cplusplus
 }

@@ -2,6 +2,7 @@
 // memory, staging of host reads, and the two phases of the paper's
 // algorithm (Sect. 2.4): distribution (at kmc_add_reads*) and sorting (at
 // kmc_count).
+#include <atomic>
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -107,8 +108,34 @@ int cuda_fail(cudaError_t e, const char *what) {
   return KMC_ECUDA;
 }
 
+// Allocations left before the injected failure (< 0: none is injected).
+std::atomic<int64_t> g_fail_alloc{-1};
+
+bool alloc_fault_injected() {
+  int64_t v = g_fail_alloc.load();
+  while (v >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1)) {
+      if (v == 0) {
+        snprintf(g_last_err, sizeof(g_last_err), "allocation failed (injected by kmc_debug_fail_alloc)");
+        return true;
+      }
+      return false;
+    }
+  }
+  return false;
+}
+
+cudaError_t host_alloc(void **p, size_t bytes, unsigned flags) {
+  *p = nullptr;
+  if (alloc_fault_injected()) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(p, bytes, flags);
+}
+
 int dev_ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
   if (bytes <= b.cap && b.p) return 0;
+  if (alloc_fault_injected()) {  // the buffer is left as it is: released by its owner
+    return 1;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   if (b.p) cudaFreeAsync(b.p, st);
@@ -213,7 +240,7 @@ int validate(const kmc_params *p) {
   if (!p->canonical && p->x != 0 && p->x != KMC_AUTO) return KMC_EINVAL;  // (k,x)-mers are canonical
   if (p->reserved0) return KMC_EINVAL;
   if (p->debug_flags & ~(KMC_DEBUG_KEEP_SUPERKMERS | KMC_DEBUG_KEEP_KEYS | KMC_DEBUG_NARROW_SORT |
-                         KMC_DEBUG_SIG_TILE | KMC_DEBUG_MINIMIZER))
+                         KMC_DEBUG_SIG_TILE | KMC_DEBUG_MINIMIZER | KMC_DEBUG_WAIT_TIMEOUT))
     return KMC_EINVAL;
   return KMC_OK;
 }
@@ -381,8 +408,14 @@ const char *kmc_strerror(int code) {
     case KMC_EAGAIN: return "not ready";
     case KMC_EINPUT: return "malformed read offsets";
     case KMC_EIO: return g_last_err[0] ? g_last_err : "file error";
+    case KMC_ECANCELED: return "job cancelled";
     default: return "unknown error";
   }
+}
+
+int kmc_debug_fail_alloc(int64_t after) {
+  g_fail_alloc.store(after < 0 ? -1 : after);
+  return KMC_OK;
 }
 
 int kmc_open(kmc_handle **out, const kmc_params *p) {
@@ -573,7 +606,7 @@ int kmc_add_reads(kmc_handle *kh, const char *bases, const uint64_t *offsets, ui
       const size_t slice = 64ull << 20;
       for (int i = 0; i < 2; ++i) {
         if (!ds.stage_host[i]) {
-          if (cudaHostAlloc(&ds.stage_host[i], slice, cudaHostAllocDefault) != cudaSuccess) {
+          if (host_alloc(&ds.stage_host[i], slice, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             return KMC_ENOMEM;
           }

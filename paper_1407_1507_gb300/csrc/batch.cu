@@ -229,10 +229,10 @@ struct BatchEngine {
         E(res_kmers, sv_cap * 8) || E(set_hist, (size_t)max_sets * 4 + 4) ||
         E(set_base, ((size_t)max_sets + 2) * 8))
       return KMC_ENOMEM;
-    if (cudaHostAlloc((void **)&h_in, cap_bases + 64, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&h_offs, (cap_reads + 2) * 8, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&h_set_starts, (max_sets + 2) * 8, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&h_dyn, sizeof(BatchDyn), cudaHostAllocDefault) != cudaSuccess) {
+    if (host_alloc((void **)&h_in, cap_bases + 64, cudaHostAllocDefault) != cudaSuccess ||
+        host_alloc((void **)&h_offs, (cap_reads + 2) * 8, cudaHostAllocDefault) != cudaSuccess ||
+        host_alloc((void **)&h_set_starts, (max_sets + 2) * 8, cudaHostAllocDefault) != cudaSuccess ||
+        host_alloc((void **)&h_dyn, sizeof(BatchDyn), cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       return KMC_ENOMEM;
     }

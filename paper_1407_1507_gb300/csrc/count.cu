@@ -117,6 +117,7 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
     if (dev_ensure(ss.tile_desc, ((size_t)plan.NB + 1) * sizeof(TileDesc), h.st)) return KMC_ENOMEM;
     TilePlan gplan = plan;
     gplan.desc = as<TileDesc>(ss.tile_desc);
+    gplan.debug = (h.p.debug_flags & KMC_DEBUG_WAIT_TIMEOUT) ? 1u : 0u;
     StageScope sc(h, KMC_STAGE_TILE_SORT);
     tile_desc_kernel<<<(unsigned)std::min<uint64_t>((plan.NB + 255) / 256, 4096), 256, 0, h.st>>>(
         plan, as<TileDesc>(ss.tile_desc));
@@ -359,7 +360,7 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
     if (ss.meta_host) cudaFreeHost(ss.meta_host);
     ss.meta_host = nullptr;
     ss.meta_host_cap = 0;
-    if (cudaHostAlloc(&ss.meta_host, o_up + (o_up >> 2), cudaHostAllocDefault) != cudaSuccess) {
+    if (host_alloc(&ss.meta_host, o_up + (o_up >> 2), cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       return KMC_ENOMEM;
     }

@@ -268,7 +268,7 @@ int distribute_device_piece(Handle &h, const char *piece_ptr, const uint64_t *d_
     // over the device share of the budget: the bins go to pinned host memory
     // (copied after the scatter on this stream), the sort reads them there
     void *host = nullptr;
-    if (cudaHostAlloc(&host, bytes, cudaHostAllocMapped) != cudaSuccess) {
+    if (host_alloc(&host, bytes, cudaHostAllocMapped) != cudaSuccess) {
       cudaGetLastError();
       return KMC_ENOMEM;
     }

@@ -52,6 +52,12 @@ struct DevBuf {
   size_t cap = 0;
 };
 int dev_ensure(DevBuf &b, size_t bytes, cudaStream_t st);
+// Pinned host allocation (cudaHostAlloc) through the allocation-failure hook
+// of kmc_debug_fail_alloc; returns cudaErrorMemoryAllocation when the hook
+// fires.
+cudaError_t host_alloc(void **p, size_t bytes, unsigned flags);
+// True (once) when kmc_debug_fail_alloc asked this allocation to fail.
+bool alloc_fault_injected();
 void dev_release(DevBuf &b, cudaStream_t st);
 
 template <typename T>

@@ -54,7 +54,8 @@ count_small_kernel(const uint8_t *__restrict__ bases, const uint64_t *__restrict
   __syncthreads();
   // (1) canonical k-mers (rolling forward and reverse-complement values)
   const uint64_t kmask = k == 32 ? ~0ull : ((1ull << (2 * k)) - 1);
-  for (uint64_t r = threadIdx.x; r < n_reads && !sm.bad; r += NA_THREADS) {
+  const volatile uint32_t &bad = sm.bad;  // other threads may set it: read it afresh
+  for (uint64_t r = threadIdx.x; r < n_reads && !bad; r += NA_THREADS) {
     const uint64_t a = offsets[r], e = offsets[r + 1];
     if (e < a || e > n_bases) { sm.bad = 1; break; }
     uint64_t fw = 0, rc = 0;
@@ -176,7 +177,14 @@ extern "C" int kmc_count_small_noalloc(const char *d_bases, const uint64_t *d_of
     }
     ptr = g_na_ptr[dev];
   }
+  // A k-mer in the result has count >= 1, so cutoff_min 0 keeps the same
+  // k-mers as cutoff_min 1.
   const uint64_t ci = cutoff_min ? cutoff_min : 1;
+  // An error left pending by earlier, unrelated work of this thread would
+  // otherwise be read back below as this launch's failure: report it as
+  // such, leave it pending for its owner, and launch nothing.
+  cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) return cuda_fail(pending, "error pending before count_small_kernel");
   count_small_kernel<<<1, NA_THREADS, sizeof(NaSmem), static_cast<cudaStream_t>(cuda_stream)>>>(
       reinterpret_cast<const uint8_t *>(d_bases), d_offsets, n_reads, n_bases, (int)k, ci,
       cutoff_max, static_cast<unsigned long long *>(ptr), d_kmers, d_counts, capacity, d_n_out);

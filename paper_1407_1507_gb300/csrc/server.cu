@@ -139,8 +139,15 @@ void worker(kmc_server *s, int w) {
         fp += j->footprint;
         if (nb + 64 > s->cfg.batch_bases) break;  // a large job runs alone
       }
-      if (take.empty()) {  // nothing fits the memory budget yet: wait for a batch to finish
-        s->cv_work.wait(lk, [&] { return s->stop || s->inflight == 0; });
+      if (take.empty()) {
+        // the head job does not fit the memory budget beside the batches in
+        // flight: wait until one of them finishes (or the queue changes),
+        // then check again
+        const uint64_t seen = s->n_batches;
+        const Job *head = s->queue.front();
+        s->cv_work.wait(lk, [&] {
+          return s->stop || s->n_batches != seen || s->queue.empty() || s->queue.front() != head;
+        });
         continue;
       }
       s->inflight += fp;
@@ -321,6 +328,28 @@ int kmc_server_release(kmc_server *s, uint64_t job_id) {
   if (it == s->jobs.end()) return KMC_EINVAL;
   if (it->second->status < 2 && it->second->status >= 0) return KMC_ESTATE;
   s->jobs.erase(it);
+  return KMC_OK;
+}
+
+int kmc_server_cancel(kmc_server *s, uint64_t job_id) {
+  if (!s) return KMC_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return KMC_EINVAL;
+    Job *j = it->second.get();
+    if (j->status != 0) return KMC_ESTATE;  // admitted, finished or failed
+    auto q = std::find(s->queue.begin(), s->queue.end(), j);
+    if (q == s->queue.end()) return KMC_ESTATE;
+    s->queue.erase(q);
+    j->status = KMC_ECANCELED;
+    j->t_done = now_s();
+    std::vector<char>().swap(j->bases);
+    std::vector<uint64_t>().swap(j->offsets);
+    j->offsets.push_back(0);
+  }
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();  // a worker may wait on this job as the queue's head
   return KMC_OK;
 }
 

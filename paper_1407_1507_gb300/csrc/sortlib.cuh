@@ -1,17 +1,25 @@
-// Radix-sort machinery of the sorting phase (paper Sect. 2.4: "performs
-// radix sort algorithm on them").
+// Sorting and counting machinery of the sorting phase (paper Sect. 2.4: the
+// bin's k-mers are radix sorted and equal ones counted).
 //
-// Design (GB300-first).  A bin's keys are first scattered by their top D
-// bits into digit buckets (an MSD step done by the key-building kernel);
-// consecutive buckets are packed into tiles of at most TILE keys; each tile
-// is then sorted entirely in shared memory by an LSD radix sort with 8-bit
-// digits over the bits that vary inside the tile, so every key crosses HBM
-// once in and once out.  Ranking inside a pass uses warp match (all lanes
-// with equal digits find each other in one instruction) and per-warp digit
-// counters in shared memory, scanned block-wide in (digit, warp) order,
-// which keeps every pass stable.  A bucket larger than a tile (e.g. one
-// k-mer repeated millions of times) takes a slower path: one CTA sorts it
-// with LSD passes through global memory.
+// Design (GB300-first).  A bin's keys (mixed by a bijection, so that their
+// top bits are uniform) are first partitioned by their top D bits into
+// digit buckets of about 2 k keys (the radix sweeps of kx_kernels.cuh);
+// consecutive buckets are packed into tiles of at most TILE keys, and equal
+// keys are brought together per tile in shared memory:
+//  * tile_hash_kernel (keys below 2^62, i.e. k <= 31): an open-addressing
+//    hash table per tile (64-bit CAS to claim a slot, an add to count);
+//  * tile_group_kernel (wider keys): the tile arrives by a bulk copy, one
+//    more radix step on 11 low key bits, then parallel value rounds;
+//  * tile_count_kernel: a full LSD radix sort of the tile with 8-bit digits
+//    (kept for the sorted-keys inspection and the narrow-sort check).
+// The order inside a bin does not matter: only survivors are put in global
+// order, by sort_pairs (order.cu) with the LSD tile sort below.  Ranking
+// inside an LSD pass uses warp match (lanes with equal digits find each
+// other in one instruction) and per-warp digit counters in shared memory,
+// scanned block-wide in (digit, warp) order, which keeps every pass stable.
+// A bucket larger than a tile (e.g. one k-mer repeated millions of times)
+// takes a slower path: split once more (big_group_kernel) or sorted by one
+// CTA with LSD passes through global memory (big_count_kernel).
 #pragma once
 #include <type_traits>
 #include "common.cuh"
@@ -212,6 +220,7 @@ struct TilePlan {
   uint32_t NB;                  // total buckets
   int key_bits;
   const TileDesc *desc = nullptr;  // optional: [n_tiles] ranges (tile_desc_kernel)
+  uint32_t debug = 0;              // 1: tile_group_kernel times out on purpose (failure-path check)
 };
 
 // Group holding bucket i (largest g with group_base[g] <= i).
@@ -546,6 +555,7 @@ struct TileGroupSmem {
   uint32_t ws[THREADS / 32 + 1];
   uint64_t ws64[THREADS / 32 + 1];
   uint64_t bar;                   // mbarrier of the bulk copies
+  uint64_t bar_never;             // an mbarrier nothing arrives on (failure-path check)
   unsigned long long base;
   // the tile whose copy is in flight (t_next = number of tiles when none is)
   uint32_t t_next, n_next, lead_next, group_next;
@@ -804,6 +814,7 @@ tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&s.bar, 1);
+    mbar_init(&s.bar_never, 1);
     tile_fetch<K>(keys, plan, nt, work, s, big_list, n_big, big_keys, big_cap, err);
   }
   __syncthreads();
@@ -813,8 +824,11 @@ tile_group_kernel(const K *__restrict__ keys, TilePlan plan, uint32_t *work, Cou
     const int n = (int)s.n_next, lead = (int)s.lead_next;
     const uint32_t group = s.group_next;
     // thread 0 waits for the copy; the barrier passes its result (and the
-    // copied data) on to the others, and ends the previous tile
-    const bool ok = tid != 0 || mbar_wait(&s.bar, parity);
+    // copied data) on to the others, and ends the previous tile.  The
+    // failure-path check waits (200 us at most) on a barrier that never
+    // completes instead, so that the code below runs.
+    const bool ok = tid != 0 || ((plan.debug & 1u) ? mbar_wait(&s.bar_never, 0u, 200000ull)
+                                                   : mbar_wait(&s.bar, parity));
     if (!__syncthreads_and(ok)) {
       // the copy did not land in time: report, give it one more bounded
       // wait so that no copy is left in flight, and stop

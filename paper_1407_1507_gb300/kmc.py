@@ -26,12 +26,14 @@ KMC_ETIMEOUT = -7
 KMC_EAGAIN = -8
 KMC_EINPUT = -9
 KMC_EIO = -10
+KMC_ECANCELED = -11
 KMC_AUTO = 0xFFFFFFFF
 KMC_DEBUG_KEEP_SUPERKMERS = 1
 KMC_DEBUG_KEEP_KEYS = 2
 KMC_DEBUG_NARROW_SORT = 4
 KMC_DEBUG_SIG_TILE = 8
 KMC_DEBUG_MINIMIZER = 16
+KMC_DEBUG_WAIT_TIMEOUT = 32
 KMC_FORMAT_FASTQ = 1
 KMC_FORMAT_FASTA = 2
 
@@ -167,6 +169,7 @@ SIGNATURES = [
     ("kmc_server_result", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                          _u64p, ctypes.POINTER(ctypes.c_double)]),
     ("kmc_server_release", ctypes.c_int, [_vp, ctypes.c_uint64]),
+    ("kmc_server_cancel", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("kmc_server_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_server_stats)]),
     ("kmc_server_close", None, [_vp]),
     ("kmc_db_write", ctypes.c_int, [_vp, ctypes.c_char_p]),
@@ -174,6 +177,7 @@ SIGNATURES = [
     ("kmc_db_info_get", ctypes.c_int, [_vp, ctypes.POINTER(kmc_db_info)]),
     ("kmc_db_lookup", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, _vp, _vp]),
     ("kmc_db_close", None, [_vp]),
+    ("kmc_debug_fail_alloc", ctypes.c_int, [ctypes.c_int64]),
     ("kmc_count_small_noalloc", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, ctypes.c_uint64,
                                                _vp, _vp]),
@@ -467,6 +471,18 @@ def kmc_server_result(s, job_id: int):
 
 def kmc_server_release(s, job_id: int):
     _check(load().kmc_server_release(s, job_id), "kmc_server_release")
+
+
+def kmc_server_cancel(s, job_id: int):
+    """Removes a queued job (it ends with KMC_ECANCELED); KmcError(KMC_ESTATE)
+    once it has been admitted to a batch."""
+    _check(load().kmc_server_cancel(s, job_id), "kmc_server_cancel")
+
+
+def kmc_debug_fail_alloc(after: int):
+    """Test hook: the allocation after `after` more successful ones fails once
+    (after < 0 cancels)."""
+    _check(load().kmc_debug_fail_alloc(after), "kmc_debug_fail_alloc")
 
 
 def kmc_server_stats_get(s) -> dict:

@@ -63,7 +63,7 @@ def test_strerror_names_every_code(lib):
 
 @pytest.mark.parametrize("field,value", [("k", 0), ("k", 65), ("m", 0), ("m", 12), ("n_bins", 0),
                                          ("n_bins", 65537), ("x", 4), ("canonical", 2),
-                                         ("reserved0", 1), ("debug_flags", 32)])
+                                         ("reserved0", 1), ("debug_flags", 64)])
 def test_open_rejects_bad_params_on_host(lib, field, value):
     p = kmc.kmc_default_params()
     setattr(p, field, value)

@@ -439,3 +439,73 @@ def test_prefix_class_counts_match_the_full_count(k, prefix):
     m = (fk[:, 0] >> np.uint64(2 * (k - len(prefix)))) == np.uint64(S.value(prefix))
     assert np_ == npos
     assert np.array_equal(v, fk[m, 0]) and np.array_equal(n, fc[m].astype(np.int64))
+
+
+# ------------------------------- signatures and splits against brute force
+# The C oracle finds signatures with 2-bit numbers (value and reverse-
+# complement value of each m-mer, the Sect. 2.2 rule as bit tests); the
+# string module enumerates substrings, canonicalises them as strings and
+# filters them with str.startswith / "AA" in.  Random k-mers and reads with
+# N, reads close to k long and low-complexity runs (A-rich, short periods,
+# poly-A with rare changes) exercise the rule's every branch: a minimum
+# taken before the filter, a wrong orientation or a lost sentinel would each
+# fail here.
+
+def _low_complexity(rng, n):
+    kind = rng.randrange(5)
+    if kind == 0:
+        return "".join(rng.choice("ACGT") for _ in range(n))
+    if kind == 1:  # A-rich
+        return "".join(rng.choice("AAAAAAACGT") for _ in range(n))
+    if kind == 2:  # short period
+        p = "".join(rng.choice("ACGT") for _ in range(rng.randint(1, 4)))
+        return (p * (n // len(p) + 1))[:n]
+    if kind == 3:  # poly-A / poly-T with a few changes
+        s = list(rng.choice("AT") * n)
+        for _ in range(rng.randint(0, 3)):
+            s[rng.randrange(n)] = rng.choice("ACGT")
+        return "".join(s)
+    return "".join(rng.choice("AC") for _ in range(n))  # AA / ACA starts everywhere
+
+
+_SIG_CASES = [(k, m) for m in (3, 5, 7, 9, 11) for k in (8, 21, 28, 31, 55) if m < k]
+
+
+@pytest.mark.parametrize("k,m", _SIG_CASES)
+def test_signature_matches_brute_force_strings(k, m):
+    rng = random.Random(1000 * k + m)
+    for _ in range(150):
+        s = _low_complexity(rng, k)
+        want = S.signature(s, m)
+        got = oracle.signature_of(s, m)
+        assert got == (4 ** m if want is None else S.value(want)), (s, m)
+
+
+@pytest.mark.parametrize("k,m", [(8, 3), (8, 5), (21, 5), (21, 7), (28, 7), (28, 9), (31, 9), (31, 11),
+                                 (55, 9), (55, 11)])
+def test_superkmers_match_brute_force_strings(k, m):
+    rng = random.Random(77 * k + m)
+    for _ in range(100):
+        L = rng.choice([k - 1, k, k + 1, k + rng.randint(2, 10), rng.randint(k, 3 * k + 20)])
+        read = list(_low_complexity(rng, L))
+        for _ in range(rng.choice([0, 0, 1, 3])):  # N breaks the read into segments
+            read[rng.randrange(L)] = "N"
+        read = "".join(read)
+        for use_min in (False, True):
+            got = oracle.superkmers(read, k, m, use_minimizer=use_min)
+            want = S.superkmers(read, k, m, use_minimizer=use_min)
+            assert len(got) == len(want), (read, use_min)
+            for (start, nk, sig), (sub, sig_s) in zip(got, want):
+                assert read[start:start + nk + k - 1] == sub
+                assert sig == (4 ** m if sig_s is None else S.value(sig_s))
+            # the per-position signatures agree with the split
+            if not use_min:
+                b, o = oracle.as_reads([read])
+                ps = oracle.position_sigs(b, o, k, m)
+                for p in range(L):
+                    kmer = read[p:p + k]
+                    if len(kmer) < k or "N" in kmer:
+                        assert ps[p] == oracle.NO_KMER
+                    else:
+                        sg = S.signature(kmer, m)
+                        assert ps[p] == (4 ** m if sg is None else S.value(sg))
