@@ -51,12 +51,21 @@ def parse():
                     help="bin count override (profiling a scaled workload at full-size bins)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-modes", action="store_true", help="skip the batched / served comparisons")
-    ap.add_argument("--batch-sets", type=int, default=300)
-    ap.add_argument("--batch-scale", type=float, default=0.02)
-    ap.add_argument("--served-jobs", type=int, default=300)
-    ap.add_argument("--served-rho", type=float, nargs="+", default=[0.8, 2.0],
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip the other workloads (large, x sweep, batched, served)")
+    ap.add_argument("--modes", nargs="+", default=["large", "x_sweep", "batched", "served"],
+                    choices=["large", "x_sweep", "batched", "served"])
+    ap.add_argument("--large-scale", type=float, default=1.0)
+    ap.add_argument("--large-steps", type=int, default=3)
+    ap.add_argument("--batch-sets", type=int, default=1000)
+    ap.add_argument("--batch-scale", type=float, default=0.1,
+                    help="read counts and genomes of the batched sets (1.0: the full workload)")
+    ap.add_argument("--served-jobs", type=int, default=1000)
+    ap.add_argument("--served-scale", type=float, default=0.02,
+                    help="request sizes of the served workload (1.0 with 5000 jobs: the full workload)")
+    ap.add_argument("--served-rho", type=float, nargs="+", default=[0.5, 0.8, 0.95, 1.2],
                     help="loads relative to the serial plain path's capacity")
+    ap.add_argument("--cpu-sample-reads", type=int, default=CPU_SAMPLE_READS)
     return ap.parse_args()
 
 
@@ -145,19 +154,57 @@ def workload(scale):
     return synth.mid(scale=scale)
 
 
-def cpu_baseline(w, k, ci, cx):
-    """The oracle as it stands on a bounded sample of the workload (host cores)."""
-    import oracle
-    n = min(CPU_SAMPLE_READS, w.n_reads)
-    b = w.bases[: int(w.offsets[n])]
-    o = w.offsets[: n + 1]
+_CPU_CHILD = r"""
+import json, os, resource, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+b = np.load(sys.argv[2]); o = np.load(sys.argv[3])
+k, ci, cx, threads, nr = (int(x) for x in sys.argv[4:9])
+o = o[:nr + 1]
+b = b[:int(o[-1])]
+t = time.perf_counter()
+_, _, npos = oracle.count(b, o, k, ci, cx, threads=threads, passes=1, return_npos=True)
+dt = time.perf_counter() - t
+print(json.dumps({"s": dt, "npos": npos, "rss_kb": resource.getrusage(resource.RUSAGE_SELF).ru_maxrss}))
+"""
+
+
+def cpu_baseline(w, k, ci, cx, n_reads=CPU_SAMPLE_READS):
+    """The oracle as it stands on a bounded sample of the workload, on all host
+    cores and on one, each in a child process of its own (its peak RSS is the
+    child's own); one hash-partition pass (the sample fits in memory)."""
+    n = min(n_reads, w.n_reads)
     cores = os.cpu_count() or 1
-    t = time.perf_counter()
-    _, _, npos = oracle.count(b, o, k, ci, cx, threads=cores, return_npos=True)
-    dt = time.perf_counter() - t
-    return {"value": npos / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n:,} reads of the workload ({npos:,} k-mer positions), "
-                      f"{dt:.1f} s on {cores} host threads"}
+    with tempfile.TemporaryDirectory() as td:
+        bp, op = os.path.join(td, "b.npy"), os.path.join(td, "o.npy")
+        np.save(bp, w.bases[: int(w.offsets[n])])
+        np.save(op, w.offsets[: n + 1])
+        runs = {}
+        for th, nr in ((cores, n), (1, max(1, n // 4))):
+            r = subprocess.run([sys.executable, "-c", _CPU_CHILD, ROOT, bp, op, str(k), str(ci), str(cx),
+                                str(th), str(nr)], capture_output=True, text=True, check=True)
+            runs[th] = json.loads(r.stdout.strip().splitlines()[-1])
+    a, one = runs[cores], runs[1]
+    return {"value": a["npos"] / a["s"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n:,} reads of the workload ({a['npos']:,} k-mer positions), "
+                      f"{a['s']:.1f} s on {cores} host threads",
+            "single_thread_kmers_per_s": one["npos"] / one["s"],
+            "single_thread_sample": f"first {max(1, n // 4):,} reads, {one['s']:.1f} s on 1 thread",
+            "peak_rss_mb": round(max(a["rss_kb"], one["rss_kb"]) / 1024, 1), "hash_passes": 1,
+            "cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 # Algorithmic bytes per launch of each stage (minimum traffic of the method:
@@ -298,21 +345,34 @@ def run_ours(args, rank, local_rank, world):
         e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
         e2e = {"value": job_rate(npos, world, e_ms), "unit": UNIT, "ms_per_step": round(e_ms, 3),
                "ms_per_step_median": round(float(np.median(laps)), 3), "ms_per_step_max": round(max(laps), 3),
+               "value_median": job_rate(npos, world, float(np.median(laps))),
                "h2d_bytes_per_step": int(w.bases.size + w.offsets.size * 8),
                "d2h_bytes_per_step": int(nout * (8 * words + 4))}
     kmc.kmc_close(h)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w, k, ci, cx)
     modes = None
     if rank == 0 and world == 1 and not args.no_modes:
         modes = {}
-        for name, fn in (("batched", run_batched), ("served", run_served)):
+        if "x_sweep" in args.modes:
             try:
+                modes["x_sweep"] = run_x_sweep(args, local_rank, w, d_bases, d_offs)
+            except Exception as e:  # reported, never hides the main line
+                modes["x_sweep"] = {"error": f"{type(e).__name__}: {e}"}
+    del d_bases, d_offs
+    torch.cuda.empty_cache()
+    if modes is not None:
+        for name, fn in (("large", run_large), ("batched", run_batched), ("served", run_served)):
+            if name not in args.modes:
+                continue
+            try:
+                t = time.perf_counter()
                 modes[name] = fn(args, local_rank)
+                modes[name]["mode_wall_s"] = round(time.perf_counter() - t, 1)
             except Exception as e:  # reported, never hides the main line
                 modes[name] = {"error": f"{type(e).__name__}: {e}"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, k, ci, cx, args.cpu_sample_reads)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -333,127 +393,280 @@ def run_ours(args, rank, local_rank, world):
 
 # ------------------------------------------------------------ batched / served
 
-def _mode_sets(n, scale, seed_base=0):
-    """Sets shaped like the batched workload (log-normal read counts with median
-    200 k, genomes 1-20 Mbp, L in {100,150,250}, k in {21,28,31}, 1 % errors, no
-    N), with read counts and genome sizes multiplied by `scale`."""
-    from paper_1407_1507_gb300 import synth
-    out = []
-    for i in range(n):
-        n_reads, genome, L, k = synth.batch_set_params(seed_base + i)
-        nr = max(1, int(n_reads * scale))
-        g = synth.genome_markov3(max(int(genome * scale), L + 1), synth.BASE_SEED + 10_000 + seed_base + i)
-        b, o = synth.reads(g, np.full(nr, L), 0.01, 0.0, synth.BASE_SEED + 20_000 + seed_base + i)
-        out.append((b, o, k, nr * (L - k + 1)))
-    return out
+_C1, _C2, _C3 = np.uint64(0x9E3779B97F4A7C15), np.uint64(0xC2B2AE3D27D4EB4F), np.uint64(0x165667B19E3779F9)
+
+
+def digest(kms, cnt):
+    """Order-sensitive 64-bit digests of a result (k-mers, counts) with its size:
+    equal results give equal tuples; a changed, moved or missing entry changes them."""
+    k = np.ascontiguousarray(kms).reshape(-1).astype(np.uint64, copy=False)
+    c = cnt.astype(np.uint64)
+    n = c.size
+    with np.errstate(over="ignore"):
+        idx = np.arange(n, dtype=np.uint64)
+        kw = k.reshape(n, -1) if n else k.reshape(0, 1)
+        kk = np.zeros(n, np.uint64)
+        for w in range(kw.shape[1]):
+            kk = kk * _C3 + kw[:, w]
+        a = int(np.sum(kk * _C1 + c * _C2 + idx * _C3, dtype=np.uint64))
+        b = int(np.bitwise_xor.reduce(kk ^ (c << np.uint64(40)) ^ (idx * _C1))) if n else 0
+    return (n, a, b)
 
 
 def run_batched(args, local_rank):
-    """Batched mode (kmc_batch_run, one graph-replayed launch sequence per
-    sub-batch, autotuned) against the plain loop of one kmc_open / add /
-    count / result per set, both through the public API from host memory."""
-    import torch
-    from paper_1407_1507_gb300 import kmc
-    sets = _mode_sets(args.batch_sets, args.batch_scale)
-    pos = sum(x[3] for x in sets)
-    # plain per-set loop
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    plain = []
-    for b, o, k, _ in sets:
-        with kmc.Counter(k, m=7, n_bins=64, device=local_rank) as c:
-            plain.append(c.add(b, o).count().result())
-    t_plain = time.perf_counter() - t
+    """Batched mode (kmc_batch_run: sub-batches replayed as one captured CUDA
+    graph, autotuned) against the plain per-set loop (kmc_reset / kmc_add_reads
+    / kmc_count / kmc_result on one open handle per k).  Both read the same host
+    arrays and copy every result back; both get one untimed warm-up pass over all
+    sets (allocations, staging buffers, tuning, graph capture), so the timed
+    passes compare counting, not set-up."""
+    from paper_1407_1507_gb300 import kmc, synth
+    t0 = time.perf_counter()
+    sets = synth.batch_sets(args.batch_sets, args.batch_scale)
+    gen_s = time.perf_counter() - t0
+    pos = sum(w.n_reads * max(0, int(w.offsets[1] - w.offsets[0]) - w.k + 1) for w in sets)
+    bases = sum(int(w.bases.size) for w in sets)
+    handles = {}
+    try:
+        for w in sets:
+            if w.k not in handles:
+                handles[w.k] = kmc.kmc_open(kmc.make_params(w.k, m=7, n_bins=64, device=local_rank))
+
+        def plain_pass():
+            out = []
+            for w in sets:
+                h = handles[w.k]
+                kmc.kmc_reset(h)
+                kmc.kmc_add_reads(h, w.bases, w.offsets)
+                kmc.kmc_count(h)
+                out.append(digest(*kmc.kmc_result(h, w.k)))
+            return out
+
+        plain_pass()
+        t = time.perf_counter()
+        plain = plain_pass()
+        t_plain = time.perf_counter() - t
+    finally:
+        for h in handles.values():
+            kmc.kmc_close(h)
     p = kmc.make_params(28, m=7, n_bins=64, device=local_rank)
     bh = kmc.kmc_batch_open(p, 256 << 20, 2_000_000, 512, kmc.KMC_BATCH_AUTOTUNE)
     try:
-        kmc.kmc_batch_run(bh, [(x[0], x[1]) for x in sets], [x[2] for x in sets])  # tunes + captures
+        pairs, ks = [(w.bases, w.offsets) for w in sets], [w.k for w in sets]
+        kmc.kmc_batch_run(bh, pairs, ks)  # tunes, captures
         t = time.perf_counter()
-        kmc.kmc_batch_run(bh, [(x[0], x[1]) for x in sets], [x[2] for x in sets])
+        kmc.kmc_batch_run(bh, pairs, ks)
         t_batch = time.perf_counter() - t
         st = kmc.kmc_batch_stats_get(bh)
-        same = all(np.array_equal(kmc.kmc_batch_result(bh, i)[0], plain[i][0]) and
-                   np.array_equal(kmc.kmc_batch_result(bh, i)[1], plain[i][1]) for i in range(len(sets)))
+        same = all(digest(*kmc.kmc_batch_result(bh, i)) == plain[i] for i in range(len(sets)))
     finally:
         kmc.kmc_batch_close(bh)
-    return {"workload": f"{len(sets)} sets shaped like the batched workload, read counts and genomes x{args.batch_scale}",
-            "kmer_positions": pos, "plain_kmers_per_s": pos / t_plain, "batched_kmers_per_s": pos / t_batch,
-            "speedup": t_plain / t_batch, "identical_to_plain": bool(same), "sub_batches": st["n_sub_batches"],
-            "single_path_sets": st["n_single"], "tuning": {"bins_per_set": st["bins_per_set"],
-                                                          "tile_keys": st["tile_keys"],
-                                                          "bucket_keys": st["bucket_keys"]}}
+    return {"workload": f"{len(sets)} sets of the batched workload, read counts and genomes x{args.batch_scale}",
+            "kmer_positions": pos, "bases": bases, "generation_s": round(gen_s, 2),
+            "plain_s": round(t_plain, 4), "batched_s": round(t_batch, 4),
+            "plain_kmers_per_s": pos / t_plain, "batched_kmers_per_s": pos / t_batch,
+            "speedup": t_plain / t_batch, "identical_to_plain": bool(same),
+            "plain": "one open handle per k, reset per set, pageable host input, result read back",
+            "sub_batches": st["n_sub_batches"], "single_path_sets": st["n_single"],
+            "tuning": {"bins_per_set": st["bins_per_set"], "tile_keys": st["tile_keys"],
+                       "bucket_keys": st["bucket_keys"]}}
 
 
 def run_served(args, local_rank):
     """Served mode: Poisson arrivals at load rho (relative to the serial plain
-    path's capacity), continuous batching, p50/p99 latency and aggregate
-    throughput, against serial plain execution of the same arrivals (one job at
-    a time, FIFO; its latencies follow from the measured service times)."""
-    from paper_1407_1507_gb300 import kmc
+    path's capacity, from its measured service times), continuous batching,
+    p50/p99 latency and aggregate throughput, against serial plain execution of
+    the same arrivals (one job at a time in arrival order on open handles; its
+    latencies follow from the measured service times).  Every served result is
+    compared with the plain result of the same request (64-bit digests)."""
+    from paper_1407_1507_gb300 import kmc, synth
+    t0 = time.perf_counter()
+    pools = synth.served_pools(args.served_scale)
+    reqs = [synth.served_request(i, pools, args.served_scale) for i in range(args.served_jobs)]
+    gen_s = time.perf_counter() - t0
+    pos = sum(nr * max(0, int(o[1] - o[0]) - k + 1) for b, o, k, nr in reqs)
+    handles = {}
+    svc, plain = [], []
+    try:
+        for k in (21, 28, 31):
+            handles[k] = kmc.kmc_open(kmc.make_params(k, m=7, n_bins=64, device=local_rank))
+            b, o, _, _ = reqs[0]
+            kmc.kmc_add_reads(handles[k], b, o)  # staging buffers
+            kmc.kmc_count(handles[k])
+        for b, o, k, _ in reqs:
+            h = handles[k]
+            t = time.perf_counter()
+            kmc.kmc_reset(h)
+            kmc.kmc_add_reads(h, b, o)
+            kmc.kmc_count(h)
+            res = kmc.kmc_result(h, k)
+            svc.append(time.perf_counter() - t)
+            plain.append(digest(*res))
+            del res
+    finally:
+        for h in handles.values():
+            kmc.kmc_close(h)
+    out = {"workload": f"{len(reqs)} Poisson requests, sizes and k as the batched sets (5% of 10 M reads) "
+                       f"x{args.served_scale}, reads from 16 pools", "kmer_positions": pos,
+           "bases": int(sum(b.size for b, _, _, _ in reqs)), "generation_s": round(gen_s, 2),
+           "serial_plain_total_s": round(float(np.sum(svc)), 3),
+           "serial_plain_mean_service_ms": float(np.mean(svc)) * 1e3,
+           "serial_plain_kmers_per_s": pos / float(np.sum(svc))}
     rng = np.random.default_rng(20140715)
-    jobs = _mode_sets(args.served_jobs, args.batch_scale, seed_base=5000)
-    # 5 % large jobs (10 M reads at full scale)
-    for i in range(0, len(jobs), 20):
-        b, o, k, _ = jobs[i]
-        from paper_1407_1507_gb300 import synth
-        L = int(o[1] - o[0]) if o.size > 1 else 150
-        nr = max(1, int(10_000_000 * args.batch_scale))
-        g = synth.genome_markov3(max(int(5_000_000 * args.batch_scale), L + 1), 31337 + i)
-        b2, o2 = synth.reads(g, np.full(nr, L), 0.01, 0.0, 4242 + i)
-        jobs[i] = (b2, o2, k, nr * (L - k + 1))
-    pos = sum(x[3] for x in jobs)
-    # serial plain: service times one job at a time
-    svc = []
-    for b, o, k, _ in jobs:
-        t = time.perf_counter()
-        with kmc.Counter(k, m=7, n_bins=64, device=local_rank) as c:
-            c.add(b, o).count().result()
-        svc.append(time.perf_counter() - t)
-    mean_svc = float(np.mean(svc))
-    out = {"workload": f"{len(jobs)} Poisson requests, sizes and k as the batched sets x{args.batch_scale}, "
-                       "5% large jobs", "kmer_positions": pos,
-           "serial_plain_mean_service_ms": mean_svc * 1e3}
     for rho in args.served_rho:
-        out[f"rho={rho}"] = _served_run(kmc, jobs, svc, rho, rng, local_rank, pos)
+        out[f"rho={rho}"] = _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos)
     return out
 
 
-def _served_run(kmc, jobs, svc, rho, rng, local_rank, pos):
+def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
     lam = rho / float(np.mean(svc))
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+    arrivals -= arrivals[0]
     done, lat_serial = 0.0, []
     for a, sv in zip(arrivals, svc):
-        start = max(a, done)
-        done = start + sv
+        done = max(a, done) + sv
         lat_serial.append((done - a) * 1e3)
-    serial_wall = done - arrivals[0]
+    serial_wall = done
     s = kmc.kmc_server_open(kmc.make_params(28, m=7, n_bins=64, device=local_rank),
                             batch_bases=128 << 20, batch_reads=1_000_000, batch_sets=256, n_workers=2,
                             warm_k=(21, 28, 31))
+    lat, same = [None] * len(reqs), [False] * len(reqs)
+    ids = [None] * len(reqs)
+    have = threading.Semaphore(0)
+    err = []
+
+    def collect():  # waits for the jobs in submission order and releases each at once
+        try:
+            for i in range(len(reqs)):
+                have.acquire()
+                kmc.kmc_server_wait(s, ids[i], -1.0)
+                kms, cnt, lat[i] = kmc.kmc_server_result(s, ids[i])
+                same[i] = digest(kms, cnt) == plain[i]
+                kmc.kmc_server_release(s, ids[i])
+        except Exception as e:  # reported below
+            err.append(f"{type(e).__name__}: {e}")
+
     try:
         st0 = kmc.kmc_server_stats_get(s)
+        col = threading.Thread(target=collect)
+        col.start()
+        late = 0.0
         t0 = time.perf_counter()
-        ids = []
-        for (b, o, k, _), a in zip(jobs, arrivals - arrivals[0]):
+        for i, ((b, o, k, _), a) in enumerate(zip(reqs, arrivals)):
             d = t0 + a - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            ids.append(kmc.kmc_server_submit(s, k, b, o))
-        lat = []
-        for jid in ids:
-            kmc.kmc_server_wait(s, jid, 600.0)
-            lat.append(kmc.kmc_server_result(s, jid)[2])
+            else:
+                late = max(late, -d)
+            ids[i] = kmc.kmc_server_submit_ref(s, k, b, o)
+            have.release()
+        col.join()
         wall = time.perf_counter() - t0
         st = kmc.kmc_server_stats_get(s)
     finally:
         kmc.kmc_server_close(s)
-    return {"arrival_rate_per_s": lam,
+    if err:
+        return {"error": err[0]}
+    return {"arrival_rate_per_s": lam, "served_wall_s": round(wall, 3),
             "served_kmers_per_s": pos / wall, "serial_plain_kmers_per_s": pos / serial_wall,
             "served_p50_ms": float(np.percentile(lat, 50)), "served_p99_ms": float(np.percentile(lat, 99)),
             "serial_plain_p50_ms": float(np.percentile(lat_serial, 50)),
             "serial_plain_p99_ms": float(np.percentile(lat_serial, 99)),
+            "identical_to_plain": bool(all(same)), "max_submit_lag_ms": round(late * 1e3, 3),
             "batches": st["batches"] - st0["batches"], "max_batch_jobs": st["max_batch_jobs"],
             "max_inflight_jobs": st["max_inflight_jobs"]}
+
+
+def _time_counts(kmc, torch, dev, stream, d_b, d_o, n_reads, n_bases, k, steps, **kw):
+    """Device-timed kmc_reset + kmc_add_reads_device + kmc_count on a resident
+    read set: (ms per step, per-stage ms, stats)."""
+    p = kmc.make_params(k, stream=stream.cuda_stream, device=dev.index, **kw)
+    h = kmc.kmc_open(p)
+    try:
+        def step():
+            kmc.kmc_reset(h)
+            kmc.kmc_add_reads_device(h, d_b.data_ptr(), d_o.data_ptr(), n_reads, n_bases)
+            kmc.kmc_count(h)
+        step()
+        st = kmc.kmc_stats_get(h)
+        stage = {x: 0.0 for x in kmc.STAGES}
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+            for x, v in kmc.kmc_stats_get(h)["ms_stage"].items():
+                stage[x] += v
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps, {x: v / steps for x, v in stage.items()}, st
+    finally:
+        kmc.kmc_close(h)
+
+
+def run_large(args, local_rank):
+    """The large workload at full size (300 Mbp genome, 20 M reads x 150 bp,
+    1 % errors, 0.1 % N, m = 9, 2048 bins): k = 28 (64-bit keys) and k = 55
+    (128-bit keys) with the reads resident in HBM, and the spill run (device
+    budget a quarter of the bins' bytes: bins in pinned host memory, sort in
+    waves)."""
+    import torch
+    from paper_1407_1507_gb300 import kmc, synth
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    w = synth.large(k=28, scale=args.large_scale)
+    d_b = torch.from_numpy(w.bases).to(dev)
+    d_o = torch.from_numpy(w.offsets.view(np.int64)).to(dev)
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    out = {"workload": f"large x{args.large_scale}: 300 Mbp order-3 Markov genome + repeats; 20M reads x 150 bp, "
+                       "1% substitutions, 0.1% N; m=9, 2048 bins, cutoffs [2, 1e9]"}
+    try:
+        for k in (28, 55):
+            ms, stage, st = _time_counts(kmc, torch, dev, stream, d_b, d_o, w.n_reads, int(w.bases.size), k,
+                                         args.large_steps, m=w.m, n_bins=w.n_bins, cutoff_min=w.cutoff_min,
+                                         cutoff_max=w.cutoff_max)
+            alg = stage_bytes(st, k)
+            a46 = sum(stage.get(x, 0.0) for x in ("kx_count", "kx_scatter", "tile_sort", "big_sort"))
+            minb = st["bin_bytes"] + 4 * 8 * ((k + 31) // 32) * st["n_kmer_positions"]
+            out[f"k={k}"] = {
+                "kmers_per_s": st["n_kmer_positions"] / (ms / 1e3), "ms_per_step": round(ms, 3),
+                "kmer_positions": st["n_kmer_positions"], "result_kmers": st["n_out"],
+                "distinct_kmers": st["n_distinct"], "key_bytes": 8 * ((k + 31) // 32),
+                "stages_ms": {x: round(v, 3) for x, v in stage.items() if v > 0},
+                "a4_a6_ms": round(a46, 3),
+                "a4_a6_frac_method_min": round(minb / (a46 / 1e3) / 1e9 / peak, 4) if a46 else None,
+                "a4_a6_frac_pass_bytes": round((alg["kx_count"] + alg["kx_scatter"] + alg["tile_sort"])
+                                               / (a46 / 1e3) / 1e9 / peak, 4) if a46 else None}
+            if k == 28:
+                bin_bytes = st["bin_bytes"]
+        ms, stage, st = _time_counts(kmc, torch, dev, stream, d_b, d_o, w.n_reads, int(w.bases.size), 28, 1,
+                                     m=w.m, n_bins=w.n_bins, cutoff_min=w.cutoff_min, cutoff_max=w.cutoff_max,
+                                     device_budget=max(1, bin_bytes // 4))
+        out["spill_k=28"] = {"device_budget": bin_bytes // 4, "spilled_bytes": st["spilled_bytes"],
+                             "waves": st["n_waves"], "ms_per_step": round(ms, 3),
+                             "kmers_per_s": st["n_kmer_positions"] / (ms / 1e3)}
+    finally:
+        del d_b, d_o
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_x_sweep(args, local_rank, w, d_b, d_o):
+    """Sect. 2.3's (k,x)-mers on the mid workload: sorted fraction (keys sorted
+    per k-mer position) and stage times for x = 0..3 at k = 28."""
+    import torch
+    from paper_1407_1507_gb300 import kmc
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for x in (0, 1, 2, 3):
+        ms, stage, st = _time_counts(kmc, torch, dev, stream, d_b, d_o, w.n_reads, int(w.bases.size), w.k,
+                                     2, m=w.m, n_bins=w.n_bins, x=x, cutoff_min=w.cutoff_min,
+                                     cutoff_max=w.cutoff_max)
+        out[f"x={x}"] = {"ms_per_step": round(ms, 3), "kmers_per_s": st["n_kmer_positions"] / (ms / 1e3),
+                         "sorted_fraction": round(st["n_sorted_keys"] / max(1, st["n_kmer_positions"]), 4),
+                         "stages_ms": {s: round(v, 3) for s, v in stage.items() if v > 0}}
+    return out
 
 
 def run_reference(args, rank, world):

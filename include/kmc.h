@@ -421,6 +421,12 @@ typedef struct {
 int kmc_server_open(kmc_server **s, const kmc_server_cfg *cfg);
 int kmc_server_submit(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets,
                       uint64_t n_reads, uint64_t *job_id);
+/* kmc_server_submit_ref: as kmc_server_submit without the copy: the server
+ *   reads the caller's host buffers in place, so they must stay valid and
+ *   unchanged until kmc_server_wait reports the job finished (or it is
+ *   cancelled).  Submission then costs no host copy, whatever the job size. */
+int kmc_server_submit_ref(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets,
+                          uint64_t n_reads, uint64_t *job_id);
 int kmc_server_wait(kmc_server *s, uint64_t job_id, double timeout_s);
 int kmc_server_result(kmc_server *s, uint64_t job_id, const uint64_t **kmers,
                       const uint32_t **counts, uint64_t *n, double *latency_ms);

@@ -42,7 +42,7 @@ Mixer<K> make_mixer(int key_bits) {
 template <typename K, int IPT>
 int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const Mixer<K> &mixer,
                 uint64_t ci, uint64_t cx, DevBuf &out_k, DevBuf &out_c, uint64_t *n_sv_out,
-                K *sorted_out, K *scratch = nullptr) {
+                K *sorted_out, K *scratch = nullptr, const SuperArgs *sup = nullptr) {
   SortScratch &ss = h.ss;
   using SM = TileCountSmem<K, CNT_THREADS, IPT>;
   using BSM = BigSmem<K, NoVal, CNT_THREADS, BIG_IPT>;
@@ -109,6 +109,25 @@ int count_tiles(Handle &h, const TilePlan &plan, uint64_t n_keys, K *keys, const
     tile_hash_kernel<HTHREADS, HIPT><<<(unsigned)std::max(1, hocc) * h.sm_count, HTHREADS, sizeof(HSM), h.st>>>(
         keys, gplan, c32 + 0, out, as<uint32_t>(ss.big_list), c32 + 1, c64 + 2, big_cap,
         as<uint32_t>(h.err)); KMC_COUNT_LAUNCH();
+    if (sup && sup->n_list) {
+      // the fused bins: one pass over each super bucket (same survivor list)
+      static DeviceOnce sattr;
+      if (!sattr.done()) {
+        KMC_CUDA_TRY(cudaFuncSetAttribute(super_hash_kernel<SUPER_THREADS>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(SuperHashSmem)));
+        sattr.set();
+      }
+      int socc = 0;
+      KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, super_hash_kernel<SUPER_THREADS>,
+                                                                 SUPER_THREADS, sizeof(SuperHashSmem)));
+      SuperArgs sa = *sup;
+      sa.work = c32 + 2;
+      const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)std::max(1, socc) * h.sm_count, sa.n_list);
+      super_hash_kernel<SUPER_THREADS><<<grid, SUPER_THREADS, sizeof(SuperHashSmem), h.st>>>(
+          sa, out, as<uint32_t>(h.err));
+      KMC_COUNT_LAUNCH();
+    }
   }
   if (!hashed && grouped) {
     KMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -243,7 +262,17 @@ struct SortMeta {
   uint32_t *super_hist = nullptr;              // keys per super bucket (zeroed)
   unsigned long long *super_base = nullptr;    // scan of super_hist [n_super + 1]
   unsigned long long *super_cursor = nullptr;  // keys placed per super bucket (zeroed)
+  // bins counted straight from their super buckets (super_hash_kernel)
+  const uint8_t *fused = nullptr;    // per bin, 1 if fused [bins]
+  const uint32_t *fused_list = nullptr;  // their super buckets, biggest bins first
+  uint32_t n_fused_list = 0;
 };
+
+// Bins whose super buckets hold at most kFuseMaxKeys keys (expected, 256 of
+// them) are counted by super_hash_kernel; a fused bin gets the fewest upper
+// digit bits that leave about kFuseTargetKeys keys per super bucket.
+constexpr uint64_t kFuseMaxKeys = 32768;
+constexpr uint64_t kFuseTargetKeys = 4096;
 
 // unit_keys > 0 asks for the generate + sweep path (x = 0, units of
 // unit_keys keys); it is taken when the bins' k-mers add up.
@@ -283,7 +312,7 @@ __global__ void meta_units_kernel(const uint64_t *kbase, const uint32_t *ubase, 
 
 // Only the bins of the wave [wb0, wb1) take part (the others are empty).
 int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta *m,
-               uint32_t unit_keys = 0, uint32_t wb0 = 0, uint32_t wb1 = ~0u) {
+               uint32_t unit_keys = 0, uint32_t wb0 = 0, uint32_t wb1 = ~0u, bool fuse = false) {
   SortScratch &ss = h.ss;
   const uint32_t B = h.p.n_bins;
   if (wb1 > B) wb1 = B;
@@ -292,11 +321,23 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   std::vector<uint32_t> gbase(B + 1);
   std::vector<uint8_t> gD(B);
   uint64_t NB = 0;
+  std::vector<uint8_t> fused(B, 0);
+  uint64_t bk_sum = 0;
+  for (uint32_t b = 0; b < B; ++b) bk_sum += bk[b];
+  // the generate + sweep path needs every k-mer position in the bins' counts
+  bool gen = unit_keys > 0 && !(wb0 == 0 && wb1 == B && bk_sum != h.stats.n_kmer_positions);
+  const bool may_fuse = fuse && gen;
   for (uint32_t b = 0; b < B; ++b) {
     gD[b] = (uint8_t)digits_for((uint64_t)(bk[b] * keys_per_kmer), key_bits, tile);
     // the two sweeps place at most SWEEP_BITS_MAX digit bits; bigger bins
     // get bigger buckets, which the big-tile pass splits further
     if (unit_keys) gD[b] = (uint8_t)std::min<int>(gD[b], SWEEP_BITS_MAX);
+    if (may_fuse && bk[b] && (bk[b] + 255) / 256 <= kFuseMaxKeys) {
+      int S = 0;
+      while (S < SWEEP_UPPER && S < key_bits && (bk[b] + (1ull << S) - 1) >> S > kFuseTargetKeys) ++S;
+      gD[b] = (uint8_t)S;
+      fused[b] = 1;
+    }
     gbase[b] = (uint32_t)NB;
     NB += 1ull << gD[b];
   }
@@ -306,17 +347,26 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   // first chunk.  The chunks and units themselves are written on the device.
   std::vector<uint64_t> kbase(B + 1, 0);
   std::vector<uint32_t> sbase(B + 1, 0), ubase(B + 1, 0);
-  bool gen = unit_keys > 0;
   if (gen) {
     for (uint32_t b = 0; b < B; ++b) {
       kbase[b + 1] = kbase[b] + bk[b];
       sbase[b + 1] = sbase[b] + (1u << std::min<int>(gD[b], SWEEP_UPPER));
       ubase[b + 1] = ubase[b] + (uint32_t)((bk[b] + unit_keys - 1) / unit_keys);
     }
-    if (wb0 == 0 && wb1 == B && kbase[B] != h.stats.n_kmer_positions) gen = false;
   }
   const uint32_t n_units = gen ? ubase[B] : 0;
   const uint32_t n_super = gen ? sbase[B] : 0;
+  // super buckets of the fused bins, the biggest bins first (balance)
+  std::vector<uint32_t> flist;
+  if (gen && may_fuse) {
+    std::vector<uint32_t> order;
+    for (uint32_t b = 0; b < B; ++b)
+      if (fused[b]) order.push_back(b);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return bk[x] > bk[y]; });
+    for (uint32_t b : order)
+      for (uint32_t q = sbase[b]; q < sbase[b + 1]; ++q) flist.push_back(q);
+  }
+  const uint32_t n_flist = (uint32_t)flist.size();
   const size_t P = h.pieces.size();
   std::vector<PieceDesc> pds;
   std::vector<const uint64_t *> rbp;
@@ -342,7 +392,9 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   const size_t o_ub = o_sg + up16((B + 1) * 4);
   const size_t o_cp = o_ub + up16((B + 1) * 4);
   const size_t o_rb = o_cp + up16((P * B + 1) * 4);
-  const size_t o_up = o_rb + up16((P + 1) * 8);  // device-only from here on
+  const size_t o_fu = o_rb + up16((P + 1) * 8);
+  const size_t o_fl = o_fu + up16(B + 1);
+  const size_t o_up = o_fl + up16(((size_t)n_flist + 1) * 4);  // device-only from here on
   const size_t o_ch = o_up;
   const size_t o_un = o_ch + up16(((size_t)n_chunks + 1) * sizeof(Chunk));
   const size_t o_bf = o_un + up16(((size_t)n_units + 1) * sizeof(PartUnit));
@@ -376,6 +428,8 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   memcpy(meta + o_ub, ubase.data(), (B + 1) * 4);
   memcpy(meta + o_cp, cpos.data(), (P * B + 1) * 4);
   memcpy(meta + o_rb, rbp.data(), P * 8);
+  memcpy(meta + o_fu, fused.data(), B);
+  if (n_flist) memcpy(meta + o_fl, flist.data(), (size_t)n_flist * 4);
   KMC_CUDA_TRY(cudaMemcpyAsync(ss.cursor.p, meta, o_up, cudaMemcpyHostToDevice, h.st));
   KMC_CUDA_TRY(cudaEventRecord(ss.meta_done, h.st));
   char *base = static_cast<char *>(ss.cursor.p);
@@ -395,6 +449,9 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
   m->super_hist = reinterpret_cast<uint32_t *>(base + o_sh);
   m->super_cursor = reinterpret_cast<unsigned long long *>(base + o_sc);
   m->super_base = reinterpret_cast<unsigned long long *>(base + o_sb);
+  m->fused = n_flist ? reinterpret_cast<const uint8_t *>(base + o_fu) : nullptr;
+  m->fused_list = reinterpret_cast<const uint32_t *>(base + o_fl);
+  m->n_fused_list = n_flist;
   if (n_chunks) {
     meta_chunks_kernel<<<std::min<uint32_t>((n_chunks + 255) / 256, 4096), 256, 0, h.st>>>(
         reinterpret_cast<const uint64_t *const *>(base + o_rb), reinterpret_cast<const uint32_t *>(base + o_cp),
@@ -454,7 +511,11 @@ int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_
   const int k = (int)h.p.k;
   const int key_bits = 2 * k;
   SortMeta meta;
-  int rc = build_meta(h, key_bits, TILE, 1.0, &meta, SweepTraits<K>::TILE, wb0, wb1);
+  // keys below 2^62 counted by hashing (not when the sorted keys are kept or
+  // the narrow-sort check is on) may skip the lower sweep
+  const bool fuse = sizeof(K) == 8 && key_bits <= 62 &&
+                    !(h.p.debug_flags & (KMC_DEBUG_KEEP_KEYS | KMC_DEBUG_NARROW_SORT));
+  int rc = build_meta(h, key_bits, TILE, 1.0, &meta, SweepTraits<K>::TILE, wb0, wb1, fuse);
   if (rc) return rc;
   KxArgs<K> a;
   a.n_chunks_dyn = nullptr;
@@ -506,6 +567,7 @@ int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_
     sa.n_units = (uint32_t)meta.n_units;
     sa.n_super = meta.n_super;
     sa.err = as<uint32_t>(h.err);
+    sa.fused = meta.fused;
     static DeviceOnce attr;
     if (!attr.done()) {
       KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_sweep_kernel<K, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -566,13 +628,23 @@ int sort_wave_x0(Handle &h, uint32_t wb0, uint32_t wb1, uint64_t n_keys, uint64_
   plan.n_groups = h.p.n_bins;
   plan.NB = (uint32_t)NB;
   plan.key_bits = key_bits;
+  plan.skip_group = meta.fused;
   K *sorted_out = nullptr;
   if (h.p.debug_flags & KMC_DEBUG_KEEP_KEYS) {
     if (dev_ensure(ss.sorted_keys, (n_keys + 1) * sizeof(K), h.st)) return KMC_ENOMEM;
     sorted_out = as<K>(ss.sorted_keys);
   }
+  SuperArgs sup{};
+  if (meta.gen && meta.n_fused_list) {
+    // the fused bins' keys stay where the upper sweep put them (scratch)
+    sup.keys = reinterpret_cast<const uint64_t *>(scratch);
+    sup.super_base = meta.super_base;
+    sup.list = meta.fused_list;
+    sup.n_list = meta.n_fused_list;
+  }
   rc = count_tiles<K, IPT>(h, plan, n_keys, keys, a.mixer, h.p.cutoff_min, h.p.cutoff_max,
-                           ss.sv_keys, ss.sv_counts, n_sv_out, sorted_out, scratch);
+                           ss.sv_keys, ss.sv_counts, n_sv_out, sorted_out, scratch,
+                           sup.n_list ? &sup : nullptr);
   if (rc) return rc;
   uint32_t nt = 0;
   KMC_CUDA_TRY(cudaMemcpyAsync(&nt, n_tiles_dev, 4, cudaMemcpyDeviceToHost, h.st));

@@ -390,6 +390,7 @@ struct SweepArgs {
   uint32_t n_units;
   uint32_t n_super;
   uint32_t *err;
+  const uint8_t *fused = nullptr;        // MODE 1: bins counted straight from their super buckets
 };
 
 // One tile of n keys at in[st ..]: digits (MODE 0 upper, MODE 1 lower),
@@ -491,6 +492,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 2) kx0_sweep_kernel(SweepArgs<K
     const int S = D < SWEEP_UPPER ? D : SWEEP_UPPER;
     const int E = D - S;
     const uint64_t st = a.super_base[sb], en = a.super_base[sb + 1];
+    if (a.fused && a.fused[bin]) {
+      // the bin has no lower digit (E = 0) and its super buckets are counted
+      // in place by super_hash_kernel: only the bucket size is recorded
+      if (tid == 0) a.fine_hist[a.group_base[bin] + (sb - a.sgroup_base[bin])] = (uint32_t)(en - st);
+      return;
+    }
     // histogram of the lower digits over the whole super bucket
     for (int i = tid; i < (1 << E); i += SWEEP_THREADS) s.h[i] = 0;
     __syncthreads();

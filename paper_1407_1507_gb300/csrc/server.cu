@@ -36,8 +36,11 @@ double now_s() {
 struct Job {
   uint64_t id = 0;
   uint32_t k = 0;
-  std::vector<char> bases;
+  std::vector<char> bases;        // the job's own copy of its reads (kmc_server_submit) ...
   std::vector<uint64_t> offsets;
+  const char *bp = nullptr;       // ... or the caller's buffers (kmc_server_submit_ref)
+  const uint64_t *op = nullptr;
+  uint64_t n_bases = 0;
   uint64_t n_reads = 0;
   uint64_t footprint = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
@@ -76,7 +79,7 @@ namespace {
 bool fits(const kmc_server &s, const std::vector<Job *> &take, uint64_t nb, uint64_t nr, uint64_t fp,
           const Job &j) {
   const kmc_server_cfg &c = s.cfg;
-  const uint64_t jb = j.offsets.back();
+  const uint64_t jb = j.n_bases;
   if (s.inflight + fp + j.footprint > c.mem_budget && !(take.empty() && s.inflight == 0)) return false;
   if (take.empty()) return true;  // a job always fits an empty batch (large ones run alone)
   if (take.size() >= c.batch_sets) return false;
@@ -134,7 +137,7 @@ void worker(kmc_server *s, int w) {
         if (!fits(*s, take, nb, nr, fp, *j)) break;
         take.push_back(j);
         s->queue.pop_front();
-        nb += j->offsets.back();
+        nb += j->n_bases;
         nr += j->n_reads;
         fp += j->footprint;
         if (nb + 64 > s->cfg.batch_bases) break;  // a large job runs alone
@@ -164,8 +167,8 @@ void worker(kmc_server *s, int w) {
     std::vector<uint64_t> nr;
     std::vector<uint32_t> ks;
     for (Job *j : take) {
-      bp.push_back(j->bases.data());
-      op.push_back(j->offsets.data());
+      bp.push_back(j->bp);
+      op.push_back(j->op);
       nr.push_back(j->n_reads);
       ks.push_back(j->k);
     }
@@ -200,7 +203,8 @@ void worker(kmc_server *s, int w) {
         }
         std::vector<char>().swap(j->bases);  // the reads are no longer needed
         std::vector<uint64_t>().swap(j->offsets);
-        j->offsets.push_back(0);
+        j->bp = nullptr;
+        j->op = nullptr;
       }
       s->inflight -= fp;
       s->inflight_jobs -= take.size();
@@ -265,8 +269,9 @@ int kmc_server_open(kmc_server **out, const kmc_server_cfg *cfg) {
   return KMC_OK;
 }
 
-int kmc_server_submit(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets,
-                      uint64_t n_reads, uint64_t *job_id) {
+namespace {
+int submit_job(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets, uint64_t n_reads,
+               uint64_t *job_id, bool copy) {
   if (!s || !offsets || !job_id || k < 1 || k > 32) return KMC_EINVAL;
   if (offsets[0] != 0) return KMC_EINPUT;
   for (uint64_t r = 0; r < n_reads; ++r)
@@ -275,8 +280,16 @@ int kmc_server_submit(kmc_server *s, uint32_t k, const char *bases, const uint64
   if (nb && !bases) return KMC_EINVAL;
   auto j = std::make_unique<Job>();
   j->k = k;
-  j->bases.assign(bases, bases + nb);
-  j->offsets.assign(offsets, offsets + n_reads + 1);
+  if (copy) {
+    j->bases.assign(bases, bases + nb);
+    j->offsets.assign(offsets, offsets + n_reads + 1);
+    j->bp = j->bases.data();
+    j->op = j->offsets.data();
+  } else {
+    j->bp = bases;
+    j->op = offsets;
+  }
+  j->n_bases = nb;
   j->n_reads = n_reads;
   j->footprint = kFootprintPerBase * (nb + 64);
   {
@@ -291,6 +304,17 @@ int kmc_server_submit(kmc_server *s, uint32_t k, const char *bases, const uint64
   }
   s->cv_work.notify_one();
   return KMC_OK;
+}
+}  // namespace
+
+int kmc_server_submit(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets,
+                      uint64_t n_reads, uint64_t *job_id) {
+  return submit_job(s, k, bases, offsets, n_reads, job_id, true);
+}
+
+int kmc_server_submit_ref(kmc_server *s, uint32_t k, const char *bases, const uint64_t *offsets,
+                          uint64_t n_reads, uint64_t *job_id) {
+  return submit_job(s, k, bases, offsets, n_reads, job_id, false);
 }
 
 int kmc_server_wait(kmc_server *s, uint64_t job_id, double timeout_s) {
@@ -346,7 +370,8 @@ int kmc_server_cancel(kmc_server *s, uint64_t job_id) {
     j->t_done = now_s();
     std::vector<char>().swap(j->bases);
     std::vector<uint64_t>().swap(j->offsets);
-    j->offsets.push_back(0);
+    j->bp = nullptr;
+    j->op = nullptr;
   }
   s->cv_done.notify_all();
   s->cv_work.notify_all();  // a worker may wait on this job as the queue's head

@@ -221,6 +221,7 @@ struct TilePlan {
   int key_bits;
   const TileDesc *desc = nullptr;  // optional: [n_tiles] ranges (tile_desc_kernel)
   uint32_t debug = 0;              // 1: tile_group_kernel times out on purpose (failure-path check)
+  const uint8_t *skip_group = nullptr;  // optional: groups counted elsewhere (their tiles get n = 0)
 };
 
 // Group holding bucket i (largest g with group_base[g] <= i).
@@ -256,7 +257,8 @@ static __global__ void tile_desc_kernel(TilePlan plan, TileDesc *desc) {
     int nbits;
     uint32_t group;
     tile_range(plan, t, nt, &st, &en, &nbits, &group);
-    const uint64_t n = en - st;
+    uint64_t n = en - st;
+    if (plan.skip_group && plan.skip_group[group]) n = 0;  // counted by super_hash_kernel
     desc[t] = {st, n > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)n, group};
   }
 }
@@ -979,6 +981,156 @@ tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *wor
       }
     }
     __syncthreads();  // the slots are clear and the next tile is claimed
+  }
+  const unsigned long long nd = __reduce_add_sync(FULL, (unsigned)n_distinct);
+  if (lane == 0 && nd) atomicAdd(out.n_distinct, nd);
+}
+
+// ------------------------------------------------ hashed count of super buckets
+// For bins whose super buckets (the upper radix sweep's output) hold at most
+// a few ten thousand keys, the lower sweep and the tile count are replaced
+// by one pass over each super bucket: a CTA claims a super bucket and counts
+// its keys (mixed, below 2^62) in an open-addressing table in shared memory
+// (linear probing from the key's low bits, a 64-bit CAS to claim a slot, an
+// add to count), then emits the slots whose count is inside the cutoffs.
+// Every key is read once from HBM and nothing is written but the survivors.
+// A super bucket with more distinct keys than SUPER_LIMIT is counted in P
+// passes instead (P = 2, 4, ...; pass p takes the keys whose multiplicative
+// hash selects p, so that all copies of a key fall in one pass), re-reading
+// it, mostly from L2.
+constexpr int SUPER_THREADS = 512;
+constexpr int SUPER_SLOTS = 8192;
+constexpr int SUPER_LIMIT = SUPER_SLOTS * 3 / 4;  // + SUPER_THREADS in flight < SUPER_SLOTS
+constexpr int SUPER_UNROLL = 8;
+constexpr uint32_t SUPER_MAX_PASSES = 1u << 16;
+
+struct SuperHashSmem {
+  unsigned long long tk[SUPER_SLOTS];  // slot keys (kHashEmpty when free)
+  uint32_t tc[SUPER_SLOTS];            // slot counts
+  uint32_t n_used;                     // slots claimed in this pass
+  uint32_t sb;                         // super bucket being counted
+};
+
+struct SuperArgs {
+  const uint64_t *keys;                   // the upper sweep's output
+  const unsigned long long *super_base;   // first key of each super bucket [n_super + 1]
+  const uint32_t *list;                   // the super buckets to count
+  uint32_t n_list;
+  uint32_t *work;                         // claim counter (zero at launch)
+};
+
+__device__ __forceinline__ uint32_t super_pass_of(uint64_t key, uint32_t P) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (P - 1u);
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 2)
+super_hash_kernel(SuperArgs a, CountOut<uint64_t> out, uint32_t *err) {
+  constexpr int SPT = SUPER_SLOTS / THREADS;
+  static_assert(SUPER_SLOTS % THREADS == 0 && SPT <= 32, "layout");
+  static_assert(SUPER_LIMIT + THREADS < SUPER_SLOTS, "probes must end");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SuperHashSmem &s = *reinterpret_cast<SuperHashSmem *>(smem_raw);
+  const int tid = threadIdx.x;
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) {
+    s.tk[q * THREADS + tid] = kHashEmpty;
+    s.tc[q * THREADS + tid] = 0;
+  }
+  unsigned long long n_distinct = 0;
+  for (;;) {
+    if (tid == 0) {
+      const uint32_t i = atomicAdd(a.work, 1u);
+      s.sb = i < a.n_list ? a.list[i] : 0xFFFFFFFFu;
+      s.n_used = 0;
+    }
+    __syncthreads();
+    const uint32_t sb = s.sb;
+    if (sb == 0xFFFFFFFFu) break;
+    const uint64_t st = a.super_base[sb], n = a.super_base[sb + 1] - st;
+    const uint64_t *src = a.keys + st;
+    uint32_t P = 1;
+    for (uint32_t p = 0; p < P;) {
+      bool over = false;
+      for (uint64_t e0 = 0; e0 < n; e0 += (uint64_t)THREADS * SUPER_UNROLL) {
+        uint64_t key[SUPER_UNROLL];
+#pragma unroll
+        for (int u = 0; u < SUPER_UNROLL; ++u) {
+          const uint64_t e = e0 + (uint64_t)u * THREADS + tid;
+          key[u] = e < n ? src[e] : kHashEmpty;
+        }
+#pragma unroll
+        for (int u = 0; u < SUPER_UNROLL; ++u) {
+          if (key[u] == kHashEmpty || (P > 1 && super_pass_of(key[u], P) != p)) continue;
+          uint32_t h = (uint32_t)(((uint64_t)(uint32_t)key[u] * SUPER_SLOTS) >> 32);
+          for (;;) {  // the table never fills: at most SUPER_LIMIT + THREADS slots are taken
+            const unsigned long long old = atomicCAS(&s.tk[h], kHashEmpty, key[u]);
+            if (old == kHashEmpty) {
+              atomicAdd(&s.n_used, 1u);
+              break;
+            }
+            if (old == key[u]) break;
+            h = h + 1 == (uint32_t)SUPER_SLOTS ? 0u : h + 1;
+          }
+          atomicAdd(&s.tc[h], 1u);
+        }
+        // every thread stops after the same batch once the table is too full
+        over = __syncthreads_or(*(volatile uint32_t *)&s.n_used > (uint32_t)SUPER_LIMIT);
+        if (over) break;
+      }
+      if (over) {
+        // too many distinct keys for one pass: clear, double the passes, restart
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+          s.tk[q * THREADS + tid] = kHashEmpty;
+          s.tc[q * THREADS + tid] = 0;
+        }
+        if (tid == 0) s.n_used = 0;
+        P *= 2;
+        p = 0;
+        __syncthreads();
+        if (P > SUPER_MAX_PASSES) {  // cannot happen for a bucket below 2^32 keys
+          if (tid == 0) atomicOr(err, ERR_CAPACITY);
+          break;
+        }
+        continue;
+      }
+      // occupied slots are the distinct keys of pass p: emit and clear them
+      uint32_t keep = 0;
+      uint32_t cc[SPT];
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        cc[q] = s.tc[q * THREADS + tid];
+        n_distinct += cc[q] != 0;
+        if (cc[q] >= out.ci && cc[q] <= out.cx) keep |= 1u << q;  // ci >= 1
+      }
+      const uint32_t nk = (uint32_t)__popc(keep);
+      const uint32_t incl = warp_incl_scan(nk);
+      const uint32_t wtot = __shfl_sync(FULL, incl, 31);
+      unsigned long long wbase = 0;
+      if (lane == 31 && wtot) wbase = atomicAdd(out.n, (unsigned long long)wtot);
+      wbase = __shfl_sync(FULL, wbase, 31);
+      const bool fits = wbase + wtot <= out.cap;
+      if (!fits && lane == 0) atomicOr(err, ERR_CAPACITY);
+      uint64_t q0 = wbase + incl - nk;
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        if (cc[q]) {
+          const int e = q * THREADS + tid;
+          if (fits && ((keep >> q) & 1u)) {
+            out.keys[q0] = out.mixer.unmix(s.tk[e]);
+            out.counts[q0] = cc[q];
+            ++q0;
+          }
+          s.tk[e] = kHashEmpty;
+          s.tc[e] = 0;
+        }
+      }
+      if (tid == 0) s.n_used = 0;
+      ++p;
+      __syncthreads();  // the table is clear for the next pass or bucket
+    }
   }
   const unsigned long long nd = __reduce_add_sync(FULL, (unsigned)n_distinct);
   if (lane == 0 && nd) atomicAdd(out.n_distinct, nd);

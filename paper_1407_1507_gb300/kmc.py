@@ -165,6 +165,7 @@ SIGNATURES = [
     ("kmc_batch_close", None, [_vp]),
     ("kmc_server_open", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(kmc_server_cfg)]),
     ("kmc_server_submit", ctypes.c_int, [_vp, ctypes.c_uint32, _vp, _u64p, ctypes.c_uint64, _u64p]),
+    ("kmc_server_submit_ref", ctypes.c_int, [_vp, ctypes.c_uint32, _vp, _u64p, ctypes.c_uint64, _u64p]),
     ("kmc_server_wait", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double]),
     ("kmc_server_result", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                          _u64p, ctypes.POINTER(ctypes.c_double)]),
@@ -447,6 +448,20 @@ def kmc_server_submit(s, k: int, bases: np.ndarray, offsets: np.ndarray) -> int:
     _check(load().kmc_server_submit(s, k, bases.ctypes.data if bases.size else None,
                                     _ptr(offsets, ctypes.c_uint64), offsets.size - 1, ctypes.byref(jid)),
            "kmc_server_submit")
+    return jid.value
+
+
+def kmc_server_submit_ref(s, k: int, bases: np.ndarray, offsets: np.ndarray) -> int:
+    """Zero-copy submission: the server reads `bases` and `offsets` (contiguous
+    uint8 / uint64 arrays) in place; the caller keeps them alive and unchanged
+    until the job has finished."""
+    if bases.dtype != np.uint8 or offsets.dtype != np.uint64 or not bases.flags.c_contiguous \
+            or not offsets.flags.c_contiguous:
+        raise ValueError("kmc_server_submit_ref needs contiguous uint8 bases and uint64 offsets")
+    jid = ctypes.c_uint64()
+    _check(load().kmc_server_submit_ref(s, k, bases.ctypes.data if bases.size else None,
+                                        _ptr(offsets, ctypes.c_uint64), offsets.size - 1, ctypes.byref(jid)),
+           "kmc_server_submit_ref")
     return jid.value
 
 

@@ -21,6 +21,14 @@ quick tests):
 * ``batch_set(i)``: set i of the batched workload (log-normal read count,
               median 200 k, clipped to [10 k, 5 M]; genome 1-20 Mbp; L in
               {100,150,250}; k in {21,28,31}; m=7; 1 % errors; no N).
+              ``batch_sets(n)`` builds sets 0..n-1 on several threads.
+* ``served_pools`` / ``served_request(i)``: the served workload.  Request i
+              has the batched sizes (or, with probability 0.05, 10 M reads)
+              and a k in {21,28,31}; its reads are a window of consecutive
+              reads of one of 16 read pools, each pool drawn from its own
+              genome (as a batched set's) at its own read length, so that
+              5,000 requests (about 680 Gbases) need no per-request
+              generation and no copy.
 """
 from __future__ import annotations
 
@@ -220,3 +228,63 @@ def to_fasta(bases: np.ndarray, offsets: np.ndarray, width: int = 60) -> bytes:
         for j in range(a, e, width):
             parts += [raw[j:min(e, j + width)].tobytes(), b"\n"]
     return b"".join(parts)
+
+
+def batch_sets(n: int, scale: float = 1.0, threads: int = 0, first: int = 0):
+    """Sets first..first+n-1 of the batched workload, built on `threads`
+    threads (0: all cores); the bytes are those of batch_set(i, scale)."""
+    import concurrent.futures as cf
+    nt = threads or min(16, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=nt) as ex:
+        return list(ex.map(lambda i: batch_set(i, scale), range(first, first + n)))
+
+
+SERVED_POOLS = 16
+SERVED_LARGE_READS = 10_000_000
+
+
+@dataclass
+class ReadPool:
+    bases: np.ndarray   # uint8, n_reads * L bytes
+    L: int
+    n_reads: int
+    offsets: np.ndarray  # uint64 arange(n_reads + 1) * L: the offsets of any window of it
+
+
+def served_pools(scale: float = 1.0, threads: int = 0):
+    """The 16 read pools of the served workload: pool p is n = 10 M * scale
+    reads (the largest request) of length L_p in {100, 150, 250} from its own
+    order-3 Markov genome of 1-20 Mbp (scaled), 1 % substitutions, no N."""
+    import concurrent.futures as cf
+    n = _scaled(SERVED_LARGE_READS, scale)
+
+    def one(p):
+        rng = np.random.Generator(np.random.PCG64(BASE_SEED + 14_000 + p))
+        genome = int(rng.integers(1_000_000, 20_000_001))
+        L = int(rng.choice([100, 150, 250]))
+        seed = BASE_SEED + 14_000 + p
+        g = genome_markov3(max(_scaled(genome, scale, 1000), L), seed)
+        b, o = reads(g, np.full(n, L), 0.01, 0.0, seed + 1)
+        return ReadPool(b, L, n, o)
+
+    nt = threads or min(16, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=nt) as ex:
+        return list(ex.map(one, range(SERVED_POOLS)))
+
+
+def served_request(i: int, pools, scale: float = 1.0):
+    """Request i of the served workload: (bases view, offsets view, k, n_reads).
+    Sizes as batch_set_params, but 10 M reads with probability 0.05; the reads
+    are a seeded window of one pool (views: nothing is copied)."""
+    rng = np.random.Generator(np.random.PCG64(BASE_SEED + 15_000 + i))
+    if rng.random() < 0.05:
+        nr = SERVED_LARGE_READS
+    else:
+        nr = int(np.clip(round(math.exp(math.log(200_000) + 1.0 * rng.standard_normal())), 10_000, 5_000_000))
+    k = int(rng.choice([21, 28, 31]))
+    pool = pools[int(rng.integers(0, len(pools)))]
+    nr = min(_scaled(nr, scale), pool.n_reads)
+    first = int(rng.integers(0, pool.n_reads - nr + 1))
+    L = pool.L
+    return pool.bases[first * L:(first + nr) * L], pool.offsets[:nr + 1], k, nr
+
