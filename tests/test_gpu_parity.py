@@ -71,15 +71,18 @@ def test_mid_workload_scaled(k):
     assert_same(got, oracle_count(w.bases, w.offsets, k))
 
 
-@pytest.mark.parametrize("k,ci", [(31, 1), (25, 1), (32, 1), (28, 2)])
-def test_mostly_distinct_keys_fill_the_tiles(k, ci):
+@pytest.mark.parametrize("k,ci,B", [(31, 1, 16), (25, 1, 16), (32, 1, 16), (28, 2, 16), (28, 1, 2), (21, 1, 3)])
+def test_mostly_distinct_keys_fill_the_tiles(k, ci, B):
     # iid random reads: nearly every k-mer is distinct, so the hashed tiles
-    # run close to their load limit (and k=32 takes the grouping kernel)
+    # run close to their load limit (and k=32 takes the grouping kernel);
+    # with 2 or 3 bins each bin holds millions of distinct keys, so the
+    # super buckets counted in one shared-memory pass overflow their table
+    # and are counted again in several passes
     rng = np.random.default_rng(77)
     n_reads, L = 120_000, 150
     bases = np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, n_reads * L)]
     offsets = np.arange(0, (n_reads + 1) * L, L, dtype=np.uint64)
-    got = gpu_count(bases, offsets, k, m=7, n_bins=16, cutoff_min=ci)
+    got = gpu_count(bases, offsets, k, m=7, n_bins=B, cutoff_min=ci)
     assert_same(got, oracle_count(bases, offsets, k, ci))
 
 
@@ -146,16 +149,22 @@ def test_total_count_is_number_of_positions():
 
 
 def test_heavy_repeats_take_the_big_tile_path():
-    # one read repeated 30k times: each of its k-mers has 30k copies, far above a tile
+    # one read repeated 30k times: each of its k-mers has 30k copies, far above
+    # a tile.  k = 21: the small bins are counted straight from their super
+    # buckets, where copies of a key meet in one hash slot whatever their
+    # number; k = 32 (64-bit keys, no hashing): the copies fill buckets larger
+    # than a tile, which take the big-tile path
     rng = random.Random(5)
     r = "".join(rng.choice("ACGT") for _ in range(60))
     reads = [r] * 30000 + ["A" * 80] * 2000 + rand_reads(rng, 500, 20, 120)
     b, o = oracle.as_reads(reads)
-    with kmc.Counter(21, m=7, n_bins=8) as c:
-        got = c.add(b, o).count().result()
-        st = c.stats()
-    assert st["n_big_tiles"] > 0
-    assert_same(got, oracle_count(b, o, 21))
+    for k in (21, 32):
+        with kmc.Counter(k, m=7, n_bins=8) as c:
+            got = c.add(b, o).count().result()
+            st = c.stats()
+        if k == 32:
+            assert st["n_big_tiles"] > 0
+        assert_same(got, oracle_count(b, o, k))
 
 
 def test_poly_a_and_low_complexity():
