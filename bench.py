@@ -69,6 +69,15 @@ def parse():
     return ap.parse_args()
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:8.1f} s] {msg}\n")
+    sys.stderr.flush()
+
+
 def dist_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -283,6 +292,7 @@ def run_ours(args, rank, local_rank, world):
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     clk = clocks.stop()
+    log(f"main: {ms:.2f} ms per step")
     ms = max_over_ranks(ms, world, dev)
     value = job_rate(npos, world, ms)
 
@@ -366,13 +376,16 @@ def run_ours(args, rank, local_rank, world):
                 continue
             try:
                 t = time.perf_counter()
+                log(f"mode {name} ...")
                 modes[name] = fn(args, local_rank)
                 modes[name]["mode_wall_s"] = round(time.perf_counter() - t, 1)
+                log(f"mode {name} done in {modes[name]['mode_wall_s']} s")
             except Exception as e:  # reported, never hides the main line
                 modes[name] = {"error": f"{type(e).__name__}: {e}"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, k, ci, cx, args.cpu_sample_reads)
+        log("cpu baseline done")
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -424,6 +437,7 @@ def run_batched(args, local_rank):
     t0 = time.perf_counter()
     sets = synth.batch_sets(args.batch_sets, args.batch_scale)
     gen_s = time.perf_counter() - t0
+    log(f"batched: {len(sets)} sets generated in {gen_s:.1f} s")
     pos = sum(w.n_reads * max(0, int(w.offsets[1] - w.offsets[0]) - w.k + 1) for w in sets)
     bases = sum(int(w.bases.size) for w in sets)
     handles = {}
@@ -446,6 +460,7 @@ def run_batched(args, local_rank):
         t = time.perf_counter()
         plain = plain_pass()
         t_plain = time.perf_counter() - t
+        log(f"batched: plain pass {t_plain:.2f} s")
     finally:
         for h in handles.values():
             kmc.kmc_close(h)
@@ -457,6 +472,7 @@ def run_batched(args, local_rank):
         t = time.perf_counter()
         kmc.kmc_batch_run(bh, pairs, ks)
         t_batch = time.perf_counter() - t
+        log(f"batched: batched pass {t_batch:.2f} s")
         st = kmc.kmc_batch_stats_get(bh)
         same = all(digest(*kmc.kmc_batch_result(bh, i)) == plain[i] for i in range(len(sets)))
     finally:
@@ -484,6 +500,7 @@ def run_served(args, local_rank):
     pools = synth.served_pools(args.served_scale)
     reqs = [synth.served_request(i, pools, args.served_scale) for i in range(args.served_jobs)]
     gen_s = time.perf_counter() - t0
+    log(f"served: pools and {len(reqs)} requests in {gen_s:.1f} s")
     pos = sum(nr * max(0, int(o[1] - o[0]) - k + 1) for b, o, k, nr in reqs)
     handles = {}
     svc, plain = [], []
@@ -512,9 +529,11 @@ def run_served(args, local_rank):
            "serial_plain_total_s": round(float(np.sum(svc)), 3),
            "serial_plain_mean_service_ms": float(np.mean(svc)) * 1e3,
            "serial_plain_kmers_per_s": pos / float(np.sum(svc))}
+    log(f"served: serial plain {np.sum(svc):.2f} s")
     rng = np.random.default_rng(20140715)
     for rho in args.served_rho:
         out[f"rho={rho}"] = _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos)
+        log(f"served: rho={rho} done")
     return out
 
 
@@ -539,7 +558,8 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
         try:
             for i in range(len(reqs)):
                 have.acquire()
-                kmc.kmc_server_wait(s, ids[i], -1.0)
+                if not kmc.kmc_server_wait(s, ids[i], 600.0):
+                    raise TimeoutError(f"request {i} not done after 600 s")
                 kms, cnt, lat[i] = kmc.kmc_server_result(s, ids[i])
                 same[i] = digest(kms, cnt) == plain[i]
                 kmc.kmc_server_release(s, ids[i])
@@ -639,6 +659,7 @@ def run_large(args, local_rank):
                                                / (a46 / 1e3) / 1e9 / peak, 4) if a46 else None}
             if k == 28:
                 bin_bytes = st["bin_bytes"]
+            log(f"large: k={k} {ms:.1f} ms per step")
         ms, stage, st = _time_counts(kmc, torch, dev, stream, d_b, d_o, w.n_reads, int(w.bases.size), 28, 1,
                                      m=w.m, n_bins=w.n_bins, cutoff_min=w.cutoff_min, cutoff_max=w.cutoff_max,
                                      device_budget=max(1, bin_bytes // 4))
@@ -663,6 +684,7 @@ def run_x_sweep(args, local_rank, w, d_b, d_o):
         ms, stage, st = _time_counts(kmc, torch, dev, stream, d_b, d_o, w.n_reads, int(w.bases.size), w.k,
                                      2, m=w.m, n_bins=w.n_bins, x=x, cutoff_min=w.cutoff_min,
                                      cutoff_max=w.cutoff_max)
+        log(f"x sweep: x={x} {ms:.1f} ms per step")
         out[f"x={x}"] = {"ms_per_step": round(ms, 3), "kmers_per_s": st["n_kmer_positions"] / (ms / 1e3),
                          "sorted_fraction": round(st["n_sorted_keys"] / max(1, st["n_kmer_positions"]), 4),
                          "stages_ms": {s: round(v, 3) for s, v in stage.items() if v > 0}}

@@ -482,12 +482,13 @@ int order_result(Handle &h, DevBuf &sv_k, DevBuf &sv_c, uint64_t n_sv, int k) {
   int rc = KMC_OK;
   if (n_sv) {
     StageScope sc(h, KMC_STAGE_ORDER);
-    KMC_CUDA_TRY(cudaMemcpyAsync(h.out_kmers.p, sv_k.p, n_sv * sizeof(K0), cudaMemcpyDeviceToDevice, h.st));
-    KMC_CUDA_TRY(cudaMemcpyAsync(h.out_counts.p, sv_c.p, n_sv * 4, cudaMemcpyDeviceToDevice, h.st));
+    // survivors -> result arrays in k-mer order (the survivor arrays are scratch then)
     if constexpr (sizeof(K0) == 8) {
-      rc = sort_pairs_u64(h, as<uint64_t>(h.out_kmers), as<uint32_t>(h.out_counts), n_sv, 2 * k);
+      rc = sort_pairs_to_u64(h, as<uint64_t>(sv_k), as<uint32_t>(sv_c), n_sv, 2 * k, as<uint64_t>(h.out_kmers),
+                             as<uint32_t>(h.out_counts));
     } else {
-      rc = sort_pairs_u128(h, as<u128>(h.out_kmers), as<uint32_t>(h.out_counts), n_sv, 2 * k);
+      rc = sort_pairs_to_u128(h, as<u128>(sv_k), as<uint32_t>(sv_c), n_sv, 2 * k, as<u128>(h.out_kmers),
+                              as<uint32_t>(h.out_counts));
       if (!rc) {
         swap_words_kernel<<<grid_for(n_sv, 256, 65535), 256, 0, h.st>>>(as<u128>(h.out_kmers), n_sv);
         KMC_COUNT_LAUNCH();

@@ -209,6 +209,12 @@ int debug_bin_keys(Handle &h, uint32_t bin, uint64_t *keys, uint64_t capacity, u
 // order.cu: sort (key, value) pairs in place by key bits [0, key_bits)
 int sort_pairs_u64(Handle &h, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits);
 int sort_pairs_u128(Handle &h, unsigned __int128 *keys, uint32_t *vals, uint64_t n, int key_bits);
+// Out of place: the sorted pairs go to (out_k, out_v); the input arrays are
+// used as scratch and left unspecified.
+int sort_pairs_to_u64(Handle &h, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits, uint64_t *out_k,
+                      uint32_t *out_v);
+int sort_pairs_to_u128(Handle &h, unsigned __int128 *keys, uint32_t *vals, uint64_t n, int key_bits,
+                       unsigned __int128 *out_k, uint32_t *out_v);
 
 int check_device_error(Handle &h);
 

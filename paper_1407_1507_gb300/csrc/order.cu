@@ -60,14 +60,25 @@ inline unsigned grid_for(uint64_t n, int threads, int cap = 1 << 20) {
   return (unsigned)std::min<uint64_t>(g, (uint64_t)cap);
 }
 
+// Sorts (keys, vals)[0, n) into (out_k, out_v); with out_k == keys the sort
+// is in place (through the handle's scratch).  When distinct, the input
+// arrays are clobbered (they serve as the scratch of the big buckets).
 template <typename K>
-int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits) {
+int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits, K *out_k,
+                    uint32_t *out_v) {
   using V = uint32_t;
   using SM = TilePairsSmem<K, V, PAIR_THREADS, PAIR_IPT>;
   using BSM = BigSmem<K, V, PAIR_THREADS, PAIR_BIG_IPT>;
   constexpr int TILE = PAIR_THREADS * PAIR_IPT;
   SortScratch &ss = h.ss;
-  if (n <= 1) return KMC_OK;
+  const bool in_place = out_k == keys;
+  if (n <= 1) {
+    if (n == 1 && !in_place) {
+      KMC_CUDA_TRY(cudaMemcpyAsync(out_k, keys, sizeof(K), cudaMemcpyDeviceToDevice, h.st));
+      KMC_CUDA_TRY(cudaMemcpyAsync(out_v, vals, sizeof(V), cudaMemcpyDeviceToDevice, h.st));
+    }
+    return KMC_OK;
+  }
   // many small buckets (about TILE/64 keys each): the top bits of canonical
   // k-mers are skewed, and the tile plan packs small buckets back together,
   // while a bucket above a tile would take the slow path
@@ -79,7 +90,8 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
       dev_ensure(ss.o_flag_scan, ((size_t)ND + 1) * 8, h.st) ||
       dev_ensure(ss.o_tile_first, (size_t)ND * 4 + 16, h.st) ||
       dev_ensure(ss.o_scan_tmp, scan_tmp_words(ND) * 8, h.st) ||
-      dev_ensure(ss.o_big_k, (n + 1) * sizeof(K), h.st) || dev_ensure(ss.o_big_v, (n + 1) * 4, h.st) ||
+      (in_place && (dev_ensure(ss.o_big_k, (n + 1) * sizeof(K), h.st) ||
+                    dev_ensure(ss.o_big_v, (n + 1) * 4, h.st))) ||
       dev_ensure(ss.o_cursor, 128, h.st))
     return KMC_ENOMEM;
   uint32_t *hist = as<uint32_t>(ss.o_hist);
@@ -103,8 +115,8 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
       as<uint32_t>(ss.o_flags), as<uint64_t>(ss.o_flag_scan), ND, as<uint32_t>(ss.o_tile_first), n_tiles); KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
   KMC_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)ND * 4, h.st));
-  K *tk = as<K>(ss.o_big_k);
-  V *tv = as<V>(ss.o_big_v);
+  K *tk = in_place ? as<K>(ss.o_big_k) : out_k;
+  V *tv = in_place ? as<V>(ss.o_big_v) : out_v;
   pair_scatter_kernel<K, V><<<grid_for(n, 256, 65535), 256, 0, h.st>>>(
       keys, vals, n, key_bits, D, as<uint64_t>(ss.o_base), hist, tk, tv); KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());
@@ -148,18 +160,28 @@ int sort_pairs_impl(Handle &h, K *keys, uint32_t *vals, uint64_t n, int key_bits
         tk, tv, plan, as<uint32_t>(ss.o_flags), c32 + 1, keys, vals, c64 + 1); KMC_COUNT_LAUNCH();
     KMC_CUDA_TRY(cudaGetLastError());
   }
-  KMC_CUDA_TRY(cudaMemcpyAsync(keys, tk, n * sizeof(K), cudaMemcpyDeviceToDevice, h.st));
-  KMC_CUDA_TRY(cudaMemcpyAsync(vals, tv, n * sizeof(V), cudaMemcpyDeviceToDevice, h.st));
+  if (in_place) {
+    KMC_CUDA_TRY(cudaMemcpyAsync(keys, tk, n * sizeof(K), cudaMemcpyDeviceToDevice, h.st));
+    KMC_CUDA_TRY(cudaMemcpyAsync(vals, tv, n * sizeof(V), cudaMemcpyDeviceToDevice, h.st));
+  }
   return KMC_OK;
 }
 
 }  // namespace
 
 int sort_pairs_u64(Handle &h, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits) {
-  return sort_pairs_impl<uint64_t>(h, keys, vals, n, key_bits);
+  return sort_pairs_impl<uint64_t>(h, keys, vals, n, key_bits, keys, vals);
 }
 int sort_pairs_u128(Handle &h, u128 *keys, uint32_t *vals, uint64_t n, int key_bits) {
-  return sort_pairs_impl<u128>(h, keys, vals, n, key_bits);
+  return sort_pairs_impl<u128>(h, keys, vals, n, key_bits, keys, vals);
+}
+int sort_pairs_to_u64(Handle &h, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits, uint64_t *out_k,
+                      uint32_t *out_v) {
+  return sort_pairs_impl<uint64_t>(h, keys, vals, n, key_bits, out_k, out_v);
+}
+int sort_pairs_to_u128(Handle &h, u128 *keys, uint32_t *vals, uint64_t n, int key_bits, u128 *out_k,
+                       uint32_t *out_v) {
+  return sort_pairs_impl<u128>(h, keys, vals, n, key_bits, out_k, out_v);
 }
 
 }  // namespace kmc

@@ -1000,7 +1000,7 @@ tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *wor
 // it, mostly from L2.
 constexpr int SUPER_THREADS = 512;
 constexpr int SUPER_SLOTS = 8192;
-constexpr int SUPER_LIMIT = SUPER_SLOTS * 3 / 4;  // + SUPER_THREADS in flight < SUPER_SLOTS
+constexpr int SUPER_LIMIT = SUPER_SLOTS * 3 / 4;  // checked before every insert: + SUPER_THREADS < SLOTS
 constexpr int SUPER_UNROLL = 8;
 constexpr uint32_t SUPER_MAX_PASSES = 1u << 16;
 
@@ -1060,23 +1060,42 @@ super_hash_kernel(SuperArgs a, CountOut<uint64_t> out, uint32_t *err) {
           const uint64_t e = e0 + (uint64_t)u * THREADS + tid;
           key[u] = e < n ? src[e] : kHashEmpty;
         }
+        // Every insert is preceded by a check of the slots claimed so far:
+        // a thread claims at most one slot after its check, so at most
+        // SUPER_LIMIT + THREADS slots are ever taken and a probe always
+        // finds its key or a free slot.  The probe count is bounded all the
+        // same: a probe that gives up sends the bucket to more passes.
+        bool stop = false;
 #pragma unroll
         for (int u = 0; u < SUPER_UNROLL; ++u) {
-          if (key[u] == kHashEmpty || (P > 1 && super_pass_of(key[u], P) != p)) continue;
+          if (stop || key[u] == kHashEmpty || (P > 1 && super_pass_of(key[u], P) != p)) continue;
+          if (*(volatile uint32_t *)&s.n_used > (uint32_t)SUPER_LIMIT) {
+            stop = true;
+            continue;
+          }
           uint32_t h = (uint32_t)(((uint64_t)(uint32_t)key[u] * SUPER_SLOTS) >> 32);
-          for (;;) {  // the table never fills: at most SUPER_LIMIT + THREADS slots are taken
+          bool placed = false;
+          for (int probe = 0; probe < SUPER_SLOTS; ++probe) {
             const unsigned long long old = atomicCAS(&s.tk[h], kHashEmpty, key[u]);
             if (old == kHashEmpty) {
               atomicAdd(&s.n_used, 1u);
+              placed = true;
               break;
             }
-            if (old == key[u]) break;
+            if (old == key[u]) {
+              placed = true;
+              break;
+            }
             h = h + 1 == (uint32_t)SUPER_SLOTS ? 0u : h + 1;
+          }
+          if (!placed) {
+            stop = true;
+            continue;
           }
           atomicAdd(&s.tc[h], 1u);
         }
         // every thread stops after the same batch once the table is too full
-        over = __syncthreads_or(*(volatile uint32_t *)&s.n_used > (uint32_t)SUPER_LIMIT);
+        over = __syncthreads_or(stop || *(volatile uint32_t *)&s.n_used > (uint32_t)SUPER_LIMIT);
         if (over) break;
       }
       if (over) {
