@@ -271,8 +271,14 @@ struct SortMeta {
 // Bins whose super buckets hold at most kFuseMaxKeys keys (expected, 256 of
 // them) are counted by super_hash_kernel; a fused bin gets the fewest upper
 // digit bits that leave about kFuseTargetKeys keys per super bucket.
-constexpr uint64_t kFuseMaxKeys = 32768;
-constexpr uint64_t kFuseTargetKeys = 4096;
+#ifndef KMC_FUSE_MAX_KEYS
+#define KMC_FUSE_MAX_KEYS 32768
+#endif
+#ifndef KMC_FUSE_TARGET_KEYS
+#define KMC_FUSE_TARGET_KEYS 4096
+#endif
+constexpr uint64_t kFuseMaxKeys = KMC_FUSE_MAX_KEYS;
+constexpr uint64_t kFuseTargetKeys = KMC_FUSE_TARGET_KEYS;
 
 // unit_keys > 0 asks for the generate + sweep path (x = 0, units of
 // unit_keys keys); it is taken when the bins' k-mers add up.

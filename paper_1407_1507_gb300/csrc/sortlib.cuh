@@ -994,14 +994,18 @@ tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *wor
 // (linear probing from the key's low bits, a 64-bit CAS to claim a slot, an
 // add to count), then emits the slots whose count is inside the cutoffs.
 // Every key is read once from HBM and nothing is written but the survivors.
-// A super bucket with more distinct keys than SUPER_LIMIT is counted in P
-// passes instead (P = 2, 4, ...; pass p takes the keys whose multiplicative
-// hash selects p, so that all copies of a key fall in one pass), re-reading
-// it, mostly from L2.
+// Keys go in in batches of SUPER_BATCH; a batch starts only while at most
+// SUPER_LIMIT slots are taken, so the table never fills (SUPER_LIMIT +
+// SUPER_BATCH < SUPER_SLOTS) and every probe ends.  A super bucket with more
+// distinct keys is counted in P passes instead (P = 2, 4, ...; pass p takes
+// the keys whose multiplicative hash selects p, so all copies of a key fall
+// in one pass), re-reading it, mostly from L2; a pass that overflows is split
+// in two without recounting the passes already emitted.
 constexpr int SUPER_THREADS = 512;
 constexpr int SUPER_SLOTS = 8192;
-constexpr int SUPER_LIMIT = SUPER_SLOTS * 3 / 4;  // checked before every insert: + SUPER_THREADS < SLOTS
-constexpr int SUPER_UNROLL = 8;
+constexpr int SUPER_UNROLL = 4;
+constexpr int SUPER_BATCH = SUPER_THREADS * SUPER_UNROLL;
+constexpr int SUPER_LIMIT = SUPER_SLOTS - 1 - SUPER_BATCH;
 constexpr uint32_t SUPER_MAX_PASSES = 1u << 16;
 
 struct SuperHashSmem {
@@ -1019,16 +1023,19 @@ struct SuperArgs {
   uint32_t *work;                         // claim counter (zero at launch)
 };
 
-__device__ __forceinline__ uint32_t super_pass_of(uint64_t key, uint32_t P) {
-  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (P - 1u);
+// Pass of a key when a bucket is counted in 2^lg passes: the top lg bits of
+// a multiplicative hash.  Doubling the passes splits pass q into 2q and
+// 2q + 1, so the passes already counted stay a prefix [0, 2p).
+__device__ __forceinline__ uint32_t super_pass_of(uint64_t key, int lg) {
+  return lg ? (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - lg)) : 0u;
 }
 
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 2)
 super_hash_kernel(SuperArgs a, CountOut<uint64_t> out, uint32_t *err) {
   constexpr int SPT = SUPER_SLOTS / THREADS;
-  static_assert(SUPER_SLOTS % THREADS == 0 && SPT <= 32, "layout");
-  static_assert(SUPER_LIMIT + THREADS < SUPER_SLOTS, "probes must end");
+  static_assert(THREADS == SUPER_THREADS && SUPER_SLOTS % THREADS == 0 && SPT <= 32, "layout");
+  static_assert(SUPER_LIMIT > 0 && SUPER_LIMIT + SUPER_BATCH < SUPER_SLOTS, "probes must end");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SuperHashSmem &s = *reinterpret_cast<SuperHashSmem *>(smem_raw);
   const int tid = threadIdx.x;
@@ -1050,64 +1057,63 @@ super_hash_kernel(SuperArgs a, CountOut<uint64_t> out, uint32_t *err) {
     if (sb == 0xFFFFFFFFu) break;
     const uint64_t st = a.super_base[sb], n = a.super_base[sb + 1] - st;
     const uint64_t *src = a.keys + st;
+    int lg = 0;  // the bucket is counted in P = 2^lg passes
     uint32_t P = 1;
     for (uint32_t p = 0; p < P;) {
       bool over = false;
-      for (uint64_t e0 = 0; e0 < n; e0 += (uint64_t)THREADS * SUPER_UNROLL) {
+      uint64_t nxt[SUPER_UNROLL];
+#pragma unroll
+      for (int u = 0; u < SUPER_UNROLL; ++u) {
+        const uint64_t e = (uint64_t)u * THREADS + tid;
+        nxt[u] = e < n ? src[e] : kHashEmpty;
+      }
+      for (uint64_t e0 = 0; e0 < n; e0 += SUPER_BATCH) {
         uint64_t key[SUPER_UNROLL];
 #pragma unroll
         for (int u = 0; u < SUPER_UNROLL; ++u) {
-          const uint64_t e = e0 + (uint64_t)u * THREADS + tid;
-          key[u] = e < n ? src[e] : kHashEmpty;
+          key[u] = nxt[u];
+          const uint64_t e = e0 + SUPER_BATCH + (uint64_t)u * THREADS + tid;  // next batch, in flight
+          nxt[u] = e < n ? src[e] : kHashEmpty;
         }
-        // Every insert is preceded by a check of the slots claimed so far:
-        // a thread claims at most one slot after its check, so at most
-        // SUPER_LIMIT + THREADS slots are ever taken and a probe always
-        // finds its key or a free slot.  The probe count is bounded all the
-        // same: a probe that gives up sends the bucket to more passes.
-        bool stop = false;
+        uint32_t fresh = 0;   // slots this thread claimed
+        bool lost = false;    // a probe gave up (cannot happen: SUPER_LIMIT + SUPER_BATCH < SUPER_SLOTS)
 #pragma unroll
         for (int u = 0; u < SUPER_UNROLL; ++u) {
-          if (stop || key[u] == kHashEmpty || (P > 1 && super_pass_of(key[u], P) != p)) continue;
-          if (*(volatile uint32_t *)&s.n_used > (uint32_t)SUPER_LIMIT) {
-            stop = true;
-            continue;
-          }
+          if (key[u] == kHashEmpty || (lg && super_pass_of(key[u], lg) != p)) continue;
           uint32_t h = (uint32_t)(((uint64_t)(uint32_t)key[u] * SUPER_SLOTS) >> 32);
           bool placed = false;
           for (int probe = 0; probe < SUPER_SLOTS; ++probe) {
             const unsigned long long old = atomicCAS(&s.tk[h], kHashEmpty, key[u]);
-            if (old == kHashEmpty) {
-              atomicAdd(&s.n_used, 1u);
-              placed = true;
-              break;
-            }
-            if (old == key[u]) {
+            if (old == kHashEmpty || old == key[u]) {
+              fresh += old == kHashEmpty;
               placed = true;
               break;
             }
             h = h + 1 == (uint32_t)SUPER_SLOTS ? 0u : h + 1;
           }
-          if (!placed) {
-            stop = true;
-            continue;
-          }
-          atomicAdd(&s.tc[h], 1u);
+          if (placed) atomicAdd(&s.tc[h], 1u);
+          else lost = true;
         }
-        // every thread stops after the same batch once the table is too full
-        over = __syncthreads_or(stop || *(volatile uint32_t *)&s.n_used > (uint32_t)SUPER_LIMIT);
+        // slots taken after this batch: the warp that adds last sees the total
+        const uint32_t wf = __reduce_add_sync(FULL, fresh);
+        bool full = false;
+        if (lane == 0 && wf) full = atomicAdd(&s.n_used, wf) + wf > (uint32_t)SUPER_LIMIT;
+        over = __syncthreads_or(full || lost);
         if (over) break;
       }
       if (over) {
-        // too many distinct keys for one pass: clear, double the passes, restart
+        // too many distinct keys for this pass: clear it and split it (and
+        // every later pass) in two; passes 0..p-1, already emitted, become
+        // passes 0..2p-1
 #pragma unroll
         for (int q = 0; q < SPT; ++q) {
           s.tk[q * THREADS + tid] = kHashEmpty;
           s.tc[q * THREADS + tid] = 0;
         }
         if (tid == 0) s.n_used = 0;
+        ++lg;
         P *= 2;
-        p = 0;
+        p *= 2;
         __syncthreads();
         if (P > SUPER_MAX_PASSES) {  // cannot happen for a bucket below 2^32 keys
           if (tid == 0) atomicOr(err, ERR_CAPACITY);

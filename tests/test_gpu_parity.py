@@ -86,6 +86,21 @@ def test_mostly_distinct_keys_fill_the_tiles(k, ci, B):
     assert_same(got, oracle_count(bases, offsets, k, ci))
 
 
+@pytest.mark.parametrize("n_reads", [96_000, 100_000, 104_000, 108_000])
+def test_super_buckets_split_into_passes_mid_way(n_reads):
+    # iid random reads in 4 bins: each super bucket holds about 12 k distinct
+    # keys, about twice what one pass of the shared-memory table takes, so
+    # buckets are counted in two passes and some overflow in the second one
+    # after the first was emitted; the split must not count a key twice
+    rng = np.random.default_rng(91)
+    L = 150
+    bases = np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, n_reads * L)]
+    offsets = np.arange(0, (n_reads + 1) * L, L, dtype=np.uint64)
+    for ci in (1, 2):
+        got = gpu_count(bases, offsets, 28, m=7, n_bins=4, cutoff_min=ci)
+        assert_same(got, oracle_count(bases, offsets, 28, ci))
+
+
 def test_one_bin_takes_the_wide_digit_path():
     # ~19 M k-mers in one bin need 14 digit bits, more than a unit
     # histogram holds: the partition then reserves places per warp and digit
