@@ -218,11 +218,11 @@ def _cpu_model():
 
 # Algorithmic bytes per launch of each stage (minimum traffic of the method:
 # every input read once, every output written once).
-# DRAM bytes (read + written) per key of the two sweeps (kx0_sweep_kernel on
-# 64-bit keys, both modes), from one ncu capture of the 1 M-read case
-# (--scale 0.05: 3,747.6 MB for 119,586,137 keys); the sweeps' traffic grows
-# with the keys, so it is scaled by this run's keys.
-SWEEP_DRAM_BYTES_PER_KEY_U64 = 3747.6e6 / 119586137
+# DRAM bytes (read + written) per k-mer position of a stage's kernels, from one
+# ncu capture of the 1 M-read case of the mid workload (the kernels' traffic
+# grows with the keys, so it is scaled by this run's positions); filled in for
+# the stages whose kernels were captured after their last change.
+STAGE_DRAM_BYTES_PER_KEY = {}
 
 
 def stage_bytes(st, k):
@@ -237,7 +237,9 @@ def stage_bytes(st, k):
         "signature": nb / 4 + nb / 4 + 8 * nrec,        # codes + masks in; records out
         "bin_scatter": 8 * nrec + binb / 2 + binb,      # records + bases in; bins out
         "kx_count": binb + kw * npos,                   # bins in; keys out (built once)
-        "kx_scatter": 4 * kw * npos,                    # two sweeps: keys in and out, each
+        # upper sweep over every key; lower sweep over the keys not counted
+        # straight from their super buckets: keys in and out, each
+        "kx_scatter": 2 * kw * npos + 2 * kw * (npos - st.get("n_fused_keys", 0)),
         "tile_sort": kw * npos + (kw + 4) * nout,       # keys in; survivors out
         "order": 2 * (kw + 4) * nout,                   # survivors in and out
     }
@@ -313,8 +315,8 @@ def run_ours(args, rank, local_rank, world):
     stages["sum_ms"] = round(sum(per.values()), 3)
     achieved = stages[dom]["gbs"]
     traffic = None
-    if dom == "kx_scatter" and k <= 32 and st0.get("x_used", 0) == 0:
-        traffic = int(SWEEP_DRAM_BYTES_PER_KEY_U64 * st0["n_kmer_positions"])
+    if dom in STAGE_DRAM_BYTES_PER_KEY and k <= 32 and st0.get("x_used", 0) == 0:
+        traffic = int(STAGE_DRAM_BYTES_PER_KEY[dom] * st0["n_kmer_positions"])
     roofline = {"bound": "hbm", "kernel_stage": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
@@ -406,24 +408,33 @@ def run_ours(args, rank, local_rank, world):
 
 # ------------------------------------------------------------ batched / served
 
-_C1, _C2, _C3 = np.uint64(0x9E3779B97F4A7C15), np.uint64(0xC2B2AE3D27D4EB4F), np.uint64(0x165667B19E3779F9)
-
-
 def digest(kms, cnt):
-    """Order-sensitive 64-bit digests of a result (k-mers, counts) with its size:
-    equal results give equal tuples; a changed, moved or missing entry changes them."""
-    k = np.ascontiguousarray(kms).reshape(-1).astype(np.uint64, copy=False)
-    c = cnt.astype(np.uint64)
-    n = c.size
-    with np.errstate(over="ignore"):
-        idx = np.arange(n, dtype=np.uint64)
-        kw = k.reshape(n, -1) if n else k.reshape(0, 1)
-        kk = np.zeros(n, np.uint64)
-        for w in range(kw.shape[1]):
-            kk = kk * _C3 + kw[:, w]
-        a = int(np.sum(kk * _C1 + c * _C2 + idx * _C3, dtype=np.uint64))
-        b = int(np.bitwise_xor.reduce(kk ^ (c << np.uint64(40)) ^ (idx * _C1))) if n else 0
-    return (n, a, b)
+    """Size and CRC-32s of a result's k-mers and counts: equal results give equal
+    tuples; a changed, moved or missing entry changes them (up to 2^-64)."""
+    import zlib
+    k = np.ascontiguousarray(kms)
+    c = np.ascontiguousarray(cnt)
+    return (int(c.size), zlib.crc32(memoryview(k).cast("B")) if k.size else 0,
+            zlib.crc32(memoryview(c).cast("B")) if c.size else 0)
+
+
+class PinnedOut:
+    """Reused pinned host buffers for results read back with kmc_result."""
+
+    def __init__(self):
+        self.k = self.c = None
+
+    def get(self, kmc, h, k):
+        import torch
+        n = kmc.kmc_result_size(h)
+        words = (k + 31) // 32
+        if self.k is None or self.k.size < n * words or self.c.size < n:
+            m = max(n, 1) * 2
+            self.tk = torch.empty(m * 2, dtype=torch.int64).pin_memory()
+            self.tc = torch.empty(m, dtype=torch.int32).pin_memory()
+            self.k = self.tk.numpy().view(np.uint64)
+            self.c = self.tc.numpy().view(np.uint32)
+        return kmc.kmc_result_into(h, k, self.k, self.c)
 
 
 def run_batched(args, local_rank):
@@ -446,20 +457,23 @@ def run_batched(args, local_rank):
             if w.k not in handles:
                 handles[w.k] = kmc.kmc_open(kmc.make_params(w.k, m=7, n_bins=64, device=local_rank))
 
+        po = PinnedOut()
+
         def plain_pass():
-            out = []
+            out, busy = [], 0.0
             for w in sets:
                 h = handles[w.k]
+                t = time.perf_counter()
                 kmc.kmc_reset(h)
                 kmc.kmc_add_reads(h, w.bases, w.offsets)
                 kmc.kmc_count(h)
-                out.append(digest(*kmc.kmc_result(h, w.k)))
-            return out
+                res = po.get(kmc, h, w.k)
+                busy += time.perf_counter() - t
+                out.append(digest(*res))  # outside the timed part
+            return out, busy
 
         plain_pass()
-        t = time.perf_counter()
-        plain = plain_pass()
-        t_plain = time.perf_counter() - t
+        plain, t_plain = plain_pass()
         log(f"batched: plain pass {t_plain:.2f} s")
     finally:
         for h in handles.values():
@@ -474,7 +488,7 @@ def run_batched(args, local_rank):
         t_batch = time.perf_counter() - t
         log(f"batched: batched pass {t_batch:.2f} s")
         st = kmc.kmc_batch_stats_get(bh)
-        same = all(digest(*kmc.kmc_batch_result(bh, i)) == plain[i] for i in range(len(sets)))
+        same = all(digest(*kmc.kmc_batch_result(bh, i, copy=False)) == plain[i] for i in range(len(sets)))
     finally:
         kmc.kmc_batch_close(bh)
     return {"workload": f"{len(sets)} sets of the batched workload, read counts and genomes x{args.batch_scale}",
@@ -482,7 +496,8 @@ def run_batched(args, local_rank):
             "plain_s": round(t_plain, 4), "batched_s": round(t_batch, 4),
             "plain_kmers_per_s": pos / t_plain, "batched_kmers_per_s": pos / t_batch,
             "speedup": t_plain / t_batch, "identical_to_plain": bool(same),
-            "plain": "one open handle per k, reset per set, pageable host input, result read back",
+            "plain": "one open handle per k, reset per set, pageable host input, result read back into "
+                     "reused pinned buffers; time of those calls only",
             "sub_batches": st["n_sub_batches"], "single_path_sets": st["n_single"],
             "tuning": {"bins_per_set": st["bins_per_set"], "tile_keys": st["tile_keys"],
                        "bucket_keys": st["bucket_keys"]}}
@@ -504,22 +519,24 @@ def run_served(args, local_rank):
     pos = sum(nr * max(0, int(o[1] - o[0]) - k + 1) for b, o, k, nr in reqs)
     handles = {}
     svc, plain = [], []
+    po = PinnedOut()
     try:
+        big = max(range(len(reqs)), key=lambda i: reqs[i][3])
         for k in (21, 28, 31):
             handles[k] = kmc.kmc_open(kmc.make_params(k, m=7, n_bins=64, device=local_rank))
-            b, o, _, _ = reqs[0]
-            kmc.kmc_add_reads(handles[k], b, o)  # staging buffers
+            b, o, _, _ = reqs[big]
+            kmc.kmc_add_reads(handles[k], b, o)  # staging and device buffers at their largest
             kmc.kmc_count(handles[k])
+            po.get(kmc, handles[k], k)
         for b, o, k, _ in reqs:
             h = handles[k]
             t = time.perf_counter()
             kmc.kmc_reset(h)
             kmc.kmc_add_reads(h, b, o)
             kmc.kmc_count(h)
-            res = kmc.kmc_result(h, k)
+            res = po.get(kmc, h, k)
             svc.append(time.perf_counter() - t)
-            plain.append(digest(*res))
-            del res
+            plain.append(digest(*res))  # outside the service time
     finally:
         for h in handles.values():
             kmc.kmc_close(h)
@@ -546,9 +563,10 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
         done = max(a, done) + sv
         lat_serial.append((done - a) * 1e3)
     serial_wall = done
+    # predicted device bytes in flight: up to 96 GB of the GPU's memory
     s = kmc.kmc_server_open(kmc.make_params(28, m=7, n_bins=64, device=local_rank),
                             batch_bases=128 << 20, batch_reads=1_000_000, batch_sets=256, n_workers=2,
-                            warm_k=(21, 28, 31))
+                            mem_budget=96 << 30, warm_k=(21, 28, 31))
     lat, same = [None] * len(reqs), [False] * len(reqs)
     ids = [None] * len(reqs)
     have = threading.Semaphore(0)
@@ -560,8 +578,9 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
                 have.acquire()
                 if not kmc.kmc_server_wait(s, ids[i], 600.0):
                     raise TimeoutError(f"request {i} not done after 600 s")
-                kms, cnt, lat[i] = kmc.kmc_server_result(s, ids[i])
+                kms, cnt, lat[i] = kmc.kmc_server_result(s, ids[i], copy=False)
                 same[i] = digest(kms, cnt) == plain[i]
+                del kms, cnt
                 kmc.kmc_server_release(s, ids[i])
         except Exception as e:  # reported below
             err.append(f"{type(e).__name__}: {e}")

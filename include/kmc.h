@@ -132,6 +132,8 @@ typedef struct {
   uint32_t n_waves;          /* bin waves of the last kmc_count (1 without a
                                 device_budget)                                 */
   uint32_t reserved_s;
+  uint64_t n_fused_keys;     /* keys counted straight from their super buckets
+                                (one shared-memory pass, no lower sweep)        */
 } kmc_stats;
 
 /* Stage indices of kmc_stats.ms_stage. */
@@ -380,7 +382,7 @@ void kmc_batch_close(kmc_batch *b);
  * worker threads, each with its own CUDA stream and resident batch engines
  * (kmc_batch_*), repeatedly admit queued jobs in arrival order while they
  * fit one batch (batch_bases bytes, batch_reads reads, batch_sets jobs) and
- * the device-memory budget: the predicted footprint of a job is 64 bytes
+ * the device-memory budget: the predicted footprint of a job is 32 bytes
  * per input byte, and the jobs in flight never exceed mem_budget (a job is
  * always admitted when nothing is in flight).  Jobs that arrive while
  * batches run join the next batch that has room.  A job's result is exactly
@@ -400,7 +402,7 @@ typedef struct {
   uint32_t batch_sets;   /* jobs per batch (0 = 256)                        */
   uint32_t n_workers;    /* batches in flight, 1..8 (0 = 2)                 */
   uint64_t mem_budget;   /* predicted device bytes in flight (0 = workers x
-                            64 x batch_bases)                               */
+                            32 x batch_bases)                               */
   uint32_t batch_flags;  /* KMC_BATCH_* for the workers' batch handles      */
   uint32_t reserved0;
   uint64_t warm_k_mask;  /* bit k set (1..32): every worker builds and

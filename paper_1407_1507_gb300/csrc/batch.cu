@@ -10,6 +10,7 @@
 // and split per set at the end.  Sets larger than the engine's capacity
 // take the single-set path.  An autotuner times a few settings (bins per
 // set, bucket width, tile size) on the first sub-batch and keeps the fastest.
+#include <new>
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -555,9 +556,11 @@ struct kmc_batch {
   int sm_count = 0;
   std::map<uint32_t, std::unique_ptr<BatchEngine>> engines;  // one per k, kept resident
   std::map<uint32_t, Tuning> tuned;   // tuning chosen per k
-  // results of the last run
-  std::vector<std::vector<uint64_t>> res_k;
-  std::vector<std::vector<uint32_t>> res_c;
+  // results of the last run, one host array pair per set (not zero-filled:
+  // the copies from the device write every element)
+  std::vector<BatchSetResult> res;
+  // sets above the capacity: one handle per k, kept open and reset per set
+  std::map<uint32_t, kmc_handle *> single;
   kmc_batch_stats stats{};
 };
 
@@ -665,19 +668,21 @@ int run_sub(kmc_batch *b, BatchEngine &e, const uint32_t *idx, uint32_t s0, uint
     return (errw & ERR_INPUT) ? KMC_EINPUT : (errw & ERR_OVERFLOW) ? KMC_EOVERFLOW : KMC_ECUDA;
   }
   const uint64_t n_sv = dy.n_sv;
-  std::vector<uint64_t> all_k(n_sv);
-  std::vector<uint32_t> all_c(n_sv);
-  if (n_sv) {
-    KMC_CUDA_TRY(cudaMemcpyAsync(all_k.data(), e.res_kmers.p, n_sv * 8, cudaMemcpyDeviceToHost, e.st));
-    KMC_CUDA_TRY(cudaMemcpyAsync(all_c.data(), e.ovals2.p, n_sv * 4, cudaMemcpyDeviceToHost, e.st));
-    KMC_CUDA_TRY(cudaStreamSynchronize(e.st));
-  }
+  // each set's slice of the result straight into that set's host arrays
   for (uint32_t j = s0; j < s1; ++j) {
     const uint32_t s = idx[j];
     const uint64_t a0 = sb[j - s0], a1 = sb[j - s0 + 1];
-    b->res_k[s].assign(all_k.begin() + a0, all_k.begin() + a1);
-    b->res_c[s].assign(all_c.begin() + a0, all_c.begin() + a1);
+    BatchSetResult &r = b->res[s];
+    r.n = a1 - a0;
+    r.k.reset(new (std::nothrow) uint64_t[r.n ? r.n : 1]);
+    r.c.reset(new (std::nothrow) uint32_t[r.n ? r.n : 1]);
+    if (!r.k || !r.c) return KMC_ENOMEM;
+    if (r.n) {
+      KMC_CUDA_TRY(cudaMemcpyAsync(r.k.get(), as<uint64_t>(e.res_kmers) + a0, r.n * 8, cudaMemcpyDeviceToHost, e.st));
+      KMC_CUDA_TRY(cudaMemcpyAsync(r.c.get(), as<uint32_t>(e.ovals2) + a0, r.n * 4, cudaMemcpyDeviceToHost, e.st));
+    }
   }
+  KMC_CUDA_TRY(cudaStreamSynchronize(e.st));
   b->stats.n_kmers_out += n_sv;
   return KMC_OK;
 }
@@ -728,8 +733,8 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
     for (uint64_t r = 0; r < n_reads[s]; ++r)
       if (offsets[s][r + 1] < offsets[s][r]) return KMC_EINPUT;
   }
-  b->res_k.assign(n_sets, {});
-  b->res_c.assign(n_sets, {});
+  b->res.clear();
+  b->res.resize(n_sets);
   b->stats = kmc_batch_stats{};
   const auto t_start = std::chrono::steady_clock::now();
   // sets grouped by k; large sets go through the single-set path
@@ -802,23 +807,38 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
     b->stats.bucket_keys = 256 * t.ipt / t.bucket_div;
   }
   for (uint32_t s : single) {
-    kmc_params sp = b->base;
-    sp.k = k[s];
-    sp.cuda_stream = b->st;
-    sp.x = 0;
-    kmc_handle *hh = nullptr;
-    int rc = kmc_open(&hh, &sp);
+    kmc_handle *&hh = b->single[k[s]];
+    int rc = KMC_OK;
+    if (!hh) {
+      kmc_params sp = b->base;
+      sp.k = k[s];
+      sp.cuda_stream = b->st;
+      sp.x = 0;
+      rc = kmc_open(&hh, &sp);
+      if (rc) {
+        b->single.erase(k[s]);
+        return rc;
+      }
+    } else {
+      rc = kmc_reset(hh);
+    }
     if (!rc) rc = kmc_add_reads(hh, bases[s], offsets[s], n_reads[s]);
     if (!rc) rc = kmc_count(hh);
     uint64_t n = 0;
     if (!rc) rc = kmc_result_size(hh, &n);
     if (!rc) {
-      b->res_k[s].resize(n);
-      b->res_c[s].resize(n);
-      rc = kmc_result(hh, b->res_k[s].data(), b->res_c[s].data(), n, &n);
+      BatchSetResult &r = b->res[s];
+      r.n = n;
+      r.k.reset(new (std::nothrow) uint64_t[n ? n : 1]);
+      r.c.reset(new (std::nothrow) uint32_t[n ? n : 1]);
+      if (!r.k || !r.c) rc = KMC_ENOMEM;
+      else rc = kmc_result(hh, r.k.get(), r.c.get(), n, &n);
     }
-    kmc_close(hh);
-    if (rc) return rc;
+    if (rc) {  // a failed handle is not reused
+      kmc_close(hh);
+      b->single.erase(k[s]);
+      return rc;
+    }
     b->stats.n_kmers_out += n;
     b->stats.n_single += 1;
   }
@@ -828,12 +848,25 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
 
 int kmc_batch_result(kmc_batch *b, uint32_t set, const uint64_t **kmers, const uint32_t **counts,
                      uint64_t *n) {
-  if (!b || set >= b->res_k.size()) return KMC_EINVAL;
-  if (kmers) *kmers = b->res_k[set].data();
-  if (counts) *counts = b->res_c[set].data();
-  if (n) *n = b->res_k[set].size();
+  if (!b || set >= b->res.size()) return KMC_EINVAL;
+  if (kmers) *kmers = b->res[set].k.get();
+  if (counts) *counts = b->res[set].c.get();
+  if (n) *n = b->res[set].n;
   return KMC_OK;
 }
+
+}  // extern "C"
+
+namespace kmc {
+int batch_take_result(kmc_batch *b, uint32_t set, BatchSetResult *out) {
+  if (!b || set >= b->res.size()) return KMC_EINVAL;
+  *out = std::move(b->res[set]);
+  b->res[set] = BatchSetResult{};
+  return KMC_OK;
+}
+}  // namespace kmc
+
+extern "C" {
 
 int kmc_batch_stats_get(const kmc_batch *b, kmc_batch_stats *s) {
   if (!b || !s) return KMC_EINVAL;
@@ -845,6 +878,8 @@ void kmc_batch_close(kmc_batch *b) {
   if (!b) return;
   cudaSetDevice(b->base.device);
   b->engines.clear();
+  for (auto &kv : b->single) kmc_close(kv.second);
+  b->single.clear();
   if (b->own_stream) cudaStreamDestroy(b->st);
   delete b;
 }

@@ -369,8 +369,10 @@ int build_meta(Handle &h, int key_bits, int tile, double keys_per_kmer, SortMeta
     for (uint32_t b = 0; b < B; ++b)
       if (fused[b]) order.push_back(b);
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return bk[x] > bk[y]; });
-    for (uint32_t b : order)
+    for (uint32_t b : order) {
       for (uint32_t q = sbase[b]; q < sbase[b + 1]; ++q) flist.push_back(q);
+      h.stats.n_fused_keys += bk[b];
+    }
   }
   const uint32_t n_flist = (uint32_t)flist.size();
   const size_t P = h.pieces.size();
@@ -669,6 +671,7 @@ int sort_phase_x0(Handle &h) {
   constexpr int TILE = CNT_THREADS * IPT;
   const uint32_t B = h.p.n_bins;
   h.stats.n_sorted_keys = h.stats.n_kmer_positions;
+  h.stats.n_fused_keys = 0;
   h.stats.n_big_tiles = 0;
   h.stats.n_tiles = 0;
   h.stats.x_used = 0;

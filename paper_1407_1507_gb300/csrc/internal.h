@@ -1,5 +1,6 @@
 // Host-side internals shared by the translation units of libkmc.
 #pragma once
+#include <memory>
 #include <atomic>
 #include <cstdint>
 #include <string>
@@ -207,6 +208,15 @@ int debug_bin_keys(Handle &h, uint32_t bin, uint64_t *keys, uint64_t capacity, u
                    uint32_t *words_per_key);
 
 // order.cu: sort (key, value) pairs in place by key bits [0, key_bits)
+// One set's result of a batch run, in host memory.
+struct BatchSetResult {
+  std::unique_ptr<uint64_t[]> k;
+  std::unique_ptr<uint32_t[]> c;
+  uint64_t n = 0;
+};
+// Moves set `set`'s result out of the batch handle (the handle keeps an empty one).
+int batch_take_result(kmc_batch *b, uint32_t set, BatchSetResult *out);
+
 int sort_pairs_u64(Handle &h, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits);
 int sort_pairs_u128(Handle &h, unsigned __int128 *keys, uint32_t *vals, uint64_t n, int key_bits);
 // Out of place: the sorted pairs go to (out_k, out_v); the input arrays are

@@ -26,8 +26,9 @@ namespace {
 
 // Predicted device bytes per input byte while a job is counted: the
 // distribution and sort buffers scale with the input (2-bit codes and
-// masks, super k-mer list and bins, keys, survivors).
-constexpr uint64_t kFootprintPerBase = 64;
+// masks, super k-mer list and bins about 2, the two key arrays 16 per k-mer
+// position, survivors and result up to 24 per distinct k-mer), rounded up.
+constexpr uint64_t kFootprintPerBase = 32;
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -45,8 +46,7 @@ struct Job {
   uint64_t footprint = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   int status = 0;  // 0 queued, 1 running, 2 done, < 0 error code
-  std::vector<uint64_t> kmers;
-  std::vector<uint32_t> counts;
+  BatchSetResult res;  // the k-mers and counts, moved out of the batch handle
 };
 
 }  // namespace
@@ -173,18 +173,9 @@ void worker(kmc_server *s, int w) {
       ks.push_back(j->k);
     }
     int rc = kmc_batch_run(b, (uint32_t)take.size(), bp.data(), op.data(), nr.data(), ks.data());
-    std::vector<std::vector<uint64_t>> rk(take.size());
-    std::vector<std::vector<uint32_t>> rcnt(take.size());
-    if (rc == KMC_OK) {
-      for (uint32_t i = 0; i < take.size(); ++i) {
-        const uint64_t *kp = nullptr;
-        const uint32_t *cp = nullptr;
-        uint64_t n = 0;
-        kmc_batch_result(b, i, &kp, &cp, &n);
-        rk[i].assign(kp, kp + n);
-        rcnt[i].assign(cp, cp + n);
-      }
-    }
+    std::vector<BatchSetResult> res(take.size());
+    if (rc == KMC_OK)
+      for (uint32_t i = 0; i < take.size() && rc == KMC_OK; ++i) rc = batch_take_result(b, i, &res[i]);
     {
       std::lock_guard<std::mutex> lk(s->mu);
       const double t = now_s();
@@ -192,8 +183,7 @@ void worker(kmc_server *s, int w) {
         Job *j = take[i];
         j->t_done = t;
         if (rc == KMC_OK) {
-          j->kmers.swap(rk[i]);
-          j->counts.swap(rcnt[i]);
+          j->res = std::move(res[i]);
           j->status = 2;
           s->lat_ms.push_back((j->t_done - j->t_submit) * 1e3);
           s->done += 1;
@@ -338,9 +328,9 @@ int kmc_server_result(kmc_server *s, uint64_t job_id, const uint64_t **kmers, co
   Job *j = it->second.get();
   if (j->status < 0) return j->status;
   if (j->status != 2) return KMC_EAGAIN;
-  if (kmers) *kmers = j->kmers.data();
-  if (counts) *counts = j->counts.data();
-  if (n) *n = j->kmers.size();
+  if (kmers) *kmers = j->res.k.get();
+  if (counts) *counts = j->res.c.get();
+  if (n) *n = j->res.n;
   if (latency_ms) *latency_ms = (j->t_done - j->t_submit) * 1e3;
   return KMC_OK;
 }

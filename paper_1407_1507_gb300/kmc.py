@@ -61,6 +61,7 @@ class kmc_stats(ctypes.Structure):
         ("ms_order", ctypes.c_float), ("ms_total", ctypes.c_float),
         ("ms_stage", ctypes.c_float * 12), ("n_launches", ctypes.c_uint64),
         ("spilled_bytes", ctypes.c_uint64), ("n_waves", ctypes.c_uint32), ("reserved_s", ctypes.c_uint32),
+        ("n_fused_keys", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -285,6 +286,20 @@ def kmc_result(h, k: int):
     return kms, cnt
 
 
+def kmc_result_into(h, k: int, kms_buf: np.ndarray, cnt_buf: np.ndarray):
+    """kmc_result into caller arrays (e.g. pinned host memory): kms_buf uint64
+    with at least n * ceil(k/32) elements, cnt_buf uint32 with at least n;
+    returns views of the first n k-mers and counts."""
+    n = kmc_result_size(h)
+    words = (k + 31) // 32
+    if kms_buf.size < n * words or cnt_buf.size < n:
+        raise ValueError("result buffers too small")
+    nout = ctypes.c_uint64()
+    _check(load().kmc_result(h, kms_buf.ctypes.data if n else None, cnt_buf.ctypes.data if n else None,
+                             n, ctypes.byref(nout)), "kmc_result")
+    return kms_buf[:n * words].reshape(n, words), cnt_buf[:n]
+
+
 def kmc_result_device(h):
     dk, dc, n = _vp(), _vp(), ctypes.c_uint64()
     _check(load().kmc_result_device(h, ctypes.byref(dk), ctypes.byref(dc), ctypes.byref(n)),
@@ -407,15 +422,17 @@ def kmc_batch_run(b, sets, ks):
            "kmc_batch_run")
 
 
-def kmc_batch_result(b, s: int):
+def kmc_batch_result(b, s: int, copy: bool = True):
+    """Set s's (k-mers uint64[n, 1], counts uint32[n]); copy=False returns views
+    of the handle's arrays, valid until the next kmc_batch_run or close."""
     dk, dc, n = _vp(), _vp(), ctypes.c_uint64()
     _check(load().kmc_batch_result(b, s, ctypes.byref(dk), ctypes.byref(dc), ctypes.byref(n)),
            "kmc_batch_result")
     if n.value == 0:
         return np.zeros((0, 1), np.uint64), np.zeros(0, np.uint32)
-    kms = np.ctypeslib.as_array(ctypes.cast(dk.value, _u64p), shape=(n.value,)).copy().reshape(-1, 1)
-    cnt = np.ctypeslib.as_array(ctypes.cast(dc.value, _u32p), shape=(n.value,)).copy()
-    return kms, cnt
+    kms = np.ctypeslib.as_array(ctypes.cast(dk.value, _u64p), shape=(n.value,)).reshape(-1, 1)
+    cnt = np.ctypeslib.as_array(ctypes.cast(dc.value, _u32p), shape=(n.value,))
+    return (kms.copy(), cnt.copy()) if copy else (kms, cnt)
 
 
 def kmc_batch_stats_get(b) -> dict:
@@ -473,14 +490,18 @@ def kmc_server_wait(s, job_id: int, timeout_s: float = -1.0) -> bool:
     return True
 
 
-def kmc_server_result(s, job_id: int):
+def kmc_server_result(s, job_id: int, copy: bool = True):
+    """(k-mers uint64[n, 1], counts uint32[n], latency ms) of a finished job;
+    copy=False returns views valid until kmc_server_release."""
     dk, dc, n, lat = _vp(), _vp(), ctypes.c_uint64(), ctypes.c_double()
     _check(load().kmc_server_result(s, job_id, ctypes.byref(dk), ctypes.byref(dc), ctypes.byref(n),
                                     ctypes.byref(lat)), "kmc_server_result")
     if n.value == 0:
         return np.zeros((0, 1), np.uint64), np.zeros(0, np.uint32), lat.value
-    kms = np.ctypeslib.as_array(ctypes.cast(dk.value, _u64p), shape=(n.value,)).copy().reshape(-1, 1)
-    cnt = np.ctypeslib.as_array(ctypes.cast(dc.value, _u32p), shape=(n.value,)).copy()
+    kms = np.ctypeslib.as_array(ctypes.cast(dk.value, _u64p), shape=(n.value,)).reshape(-1, 1)
+    cnt = np.ctypeslib.as_array(ctypes.cast(dc.value, _u32p), shape=(n.value,))
+    if copy:
+        kms, cnt = kms.copy(), cnt.copy()
     return kms, cnt, lat.value
 
 
