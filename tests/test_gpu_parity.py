@@ -71,13 +71,16 @@ def test_mid_workload_scaled(k):
     assert_same(got, oracle_count(w.bases, w.offsets, k))
 
 
-@pytest.mark.parametrize("k,ci,B", [(31, 1, 16), (25, 1, 16), (32, 1, 16), (28, 2, 16), (28, 1, 2), (21, 1, 3)])
+@pytest.mark.parametrize("k,ci,B", [(31, 1, 16), (25, 1, 16), (32, 1, 16), (28, 2, 16), (28, 1, 2), (21, 1, 3),
+                                    (40, 1, 16)])
 def test_mostly_distinct_keys_fill_the_tiles(k, ci, B):
     # iid random reads: nearly every k-mer is distinct, so the hashed tiles
     # run close to their load limit (and k=32 takes the grouping kernel);
     # with 2 or 3 bins each bin holds millions of distinct keys, so the
     # super buckets counted in one shared-memory pass overflow their table
-    # and are counted again in several passes
+    # and are counted again in several passes; with ci = 1 the result holds
+    # over 10 M k-mers, which the global order sorts by its two-level radix
+    # partition (64-bit keys, and 128-bit ones for k = 40)
     rng = np.random.default_rng(77)
     n_reads, L = 120_000, 150
     bases = np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, n_reads * L)]
