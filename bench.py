@@ -478,17 +478,33 @@ def run_batched(args, local_rank):
     finally:
         for h in handles.values():
             kmc.kmc_close(h)
+    # the batched calls take groups of sets of up to 4 GB of reads; each
+    # group's results are checked (untimed) before the next call reuses them
+    groups, g, gb = [], [], 0
+    for i, w in enumerate(sets):
+        if g and gb + w.bases.size > (4 << 30):
+            groups.append(g)
+            g, gb = [], 0
+        g.append(i)
+        gb += w.bases.size
+    if g:
+        groups.append(g)
     p = kmc.make_params(28, m=7, n_bins=64, device=local_rank)
     bh = kmc.kmc_batch_open(p, 256 << 20, 2_000_000, 512, kmc.KMC_BATCH_AUTOTUNE)
     try:
-        pairs, ks = [(w.bases, w.offsets) for w in sets], [w.k for w in sets]
-        kmc.kmc_batch_run(bh, pairs, ks)  # tunes, captures
-        t = time.perf_counter()
-        kmc.kmc_batch_run(bh, pairs, ks)
-        t_batch = time.perf_counter() - t
+        def batch_pass():
+            busy, ok = 0.0, True
+            for g in groups:
+                t = time.perf_counter()
+                kmc.kmc_batch_run(bh, [(sets[i].bases, sets[i].offsets) for i in g], [sets[i].k for i in g])
+                busy += time.perf_counter() - t
+                ok &= all(digest(*kmc.kmc_batch_result(bh, j, copy=False)) == plain[i] for j, i in enumerate(g))
+            return busy, ok
+
+        batch_pass()  # tunes, captures, sizes the result arena
+        t_batch, same = batch_pass()
         log(f"batched: batched pass {t_batch:.2f} s")
         st = kmc.kmc_batch_stats_get(bh)
-        same = all(digest(*kmc.kmc_batch_result(bh, i, copy=False)) == plain[i] for i in range(len(sets)))
     finally:
         kmc.kmc_batch_close(bh)
     return {"workload": f"{len(sets)} sets of the batched workload, read counts and genomes x{args.batch_scale}",
@@ -498,7 +514,9 @@ def run_batched(args, local_rank):
             "speedup": t_plain / t_batch, "identical_to_plain": bool(same),
             "plain": "one open handle per k, reset per set, pageable host input, result read back into "
                      "reused pinned buffers; time of those calls only",
-            "sub_batches": st["n_sub_batches"], "single_path_sets": st["n_single"],
+            "batched": f"{len(groups)} kmc_batch_run calls (groups of sets up to 4 GB of reads, pageable host "
+                       "input, results in the handle's pinned arena); time of those calls only",
+            "sub_batches_last_call": st["n_sub_batches"], "single_path_sets_last_call": st["n_single"],
             "tuning": {"bins_per_set": st["bins_per_set"], "tile_keys": st["tile_keys"],
                        "bucket_keys": st["bucket_keys"]}}
 
@@ -572,6 +590,19 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
     have = threading.Semaphore(0)
     err = []
 
+    got = [0]
+    stop_mon = threading.Event()
+
+    def monitor():  # progress every 10 s on stderr
+        while not stop_mon.wait(10.0):
+            try:
+                q = kmc.kmc_server_stats_get(s)
+                rss = next((ln.split()[1] for ln in open("/proc/self/status") if ln.startswith("VmRSS")), "?")
+                log(f"served rho={rho}: submitted {sum(x is not None for x in ids)}, collected {got[0]}, "
+                    f"done {q['jobs_done']}, queued {q['jobs_queued']}, rss {int(rss) // 1024} MB")
+            except Exception:
+                pass
+
     def collect():  # waits for the jobs in submission order and releases each at once
         try:
             for i in range(len(reqs)):
@@ -582,6 +613,7 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
                 same[i] = digest(kms, cnt) == plain[i]
                 del kms, cnt
                 kmc.kmc_server_release(s, ids[i])
+                got[0] += 1
         except Exception as e:  # reported below
             err.append(f"{type(e).__name__}: {e}")
 
@@ -589,6 +621,8 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
         st0 = kmc.kmc_server_stats_get(s)
         col = threading.Thread(target=collect)
         col.start()
+        mon = threading.Thread(target=monitor, daemon=True)
+        mon.start()
         late = 0.0
         t0 = time.perf_counter()
         for i, ((b, o, k, _), a) in enumerate(zip(reqs, arrivals)):
@@ -601,6 +635,7 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
             have.release()
         col.join()
         wall = time.perf_counter() - t0
+        stop_mon.set()
         st = kmc.kmc_server_stats_get(s)
     finally:
         kmc.kmc_server_close(s)

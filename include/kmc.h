@@ -350,7 +350,8 @@ int kmc_debug_bin_keys(kmc_handle *h, uint32_t bin, uint64_t *keys, uint64_t cap
  *   60 bytes per byte of capacity is allocated per k in use.
  * kmc_batch_run: counts n_sets host read sets (each as in kmc_add_reads;
  *   k[s] in 1..32).  Blocks.  Results replace those of the previous run.
- * kmc_batch_result: host arrays of set `set` (owned by the handle, valid
+ * kmc_batch_result: host arrays of set `set` (page-locked memory owned by
+ *   the handle and reused by the next run; valid
  *   until the next run or close): n k-mers (one uint64 each, layout as in
  *   kmc_result) ascending, and their counts. */
 #define KMC_BATCH_AUTOTUNE 1u

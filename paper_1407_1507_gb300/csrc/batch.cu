@@ -556,15 +556,45 @@ struct kmc_batch {
   int sm_count = 0;
   std::map<uint32_t, std::unique_ptr<BatchEngine>> engines;  // one per k, kept resident
   std::map<uint32_t, Tuning> tuned;   // tuning chosen per k
-  // results of the last run, one host array pair per set (not zero-filled:
-  // the copies from the device write every element)
-  std::vector<BatchSetResult> res;
+  // results of the last run: every set's k-mers and counts in one pinned host
+  // arena (reused across runs, grown when a run needs more), set s at
+  // [res_off[s], res_off[s] + res_n[s])
+  uint64_t *ak = nullptr;
+  uint32_t *ac = nullptr;
+  uint64_t acap = 0, aused = 0;
+  std::vector<uint64_t> res_off, res_n;
   // sets above the capacity: one handle per k, kept open and reset per set
   std::map<uint32_t, kmc_handle *> single;
   kmc_batch_stats stats{};
 };
 
 namespace {
+
+// Room for n more results in the arena (growing it keeps what is there).
+int arena_reserve(kmc_batch *b, uint64_t n) {
+  if (b->aused + n <= b->acap) return KMC_OK;
+  const uint64_t cap = std::max<uint64_t>(b->aused + n, 2 * b->acap) + (1u << 16);
+  void *nk = nullptr, *nc = nullptr;
+  if (host_alloc(&nk, cap * 8, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return KMC_ENOMEM;
+  }
+  if (host_alloc(&nc, cap * 4, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(nk);
+    return KMC_ENOMEM;
+  }
+  if (b->aused) {
+    memcpy(nk, b->ak, b->aused * 8);
+    memcpy(nc, b->ac, b->aused * 4);
+  }
+  if (b->ak) cudaFreeHost(b->ak);
+  if (b->ac) cudaFreeHost(b->ac);
+  b->ak = static_cast<uint64_t *>(nk);
+  b->ac = static_cast<uint32_t *>(nc);
+  b->acap = cap;
+  return KMC_OK;
+}
 
 int make_engine(kmc_batch *b, uint32_t k, const Tuning &t, std::unique_ptr<BatchEngine> *out) {
   auto e = std::make_unique<BatchEngine>();
@@ -668,21 +698,21 @@ int run_sub(kmc_batch *b, BatchEngine &e, const uint32_t *idx, uint32_t s0, uint
     return (errw & ERR_INPUT) ? KMC_EINPUT : (errw & ERR_OVERFLOW) ? KMC_EOVERFLOW : KMC_ECUDA;
   }
   const uint64_t n_sv = dy.n_sv;
-  // each set's slice of the result straight into that set's host arrays
+  // the sub-batch's results (set after set) into the pinned arena, one copy
+  int rc = arena_reserve(b, n_sv);
+  if (rc) return rc;
+  const uint64_t at = b->aused;
+  if (n_sv) {
+    KMC_CUDA_TRY(cudaMemcpyAsync(b->ak + at, e.res_kmers.p, n_sv * 8, cudaMemcpyDeviceToHost, e.st));
+    KMC_CUDA_TRY(cudaMemcpyAsync(b->ac + at, e.ovals2.p, n_sv * 4, cudaMemcpyDeviceToHost, e.st));
+    KMC_CUDA_TRY(cudaStreamSynchronize(e.st));
+  }
   for (uint32_t j = s0; j < s1; ++j) {
     const uint32_t s = idx[j];
-    const uint64_t a0 = sb[j - s0], a1 = sb[j - s0 + 1];
-    BatchSetResult &r = b->res[s];
-    r.n = a1 - a0;
-    r.k.reset(new (std::nothrow) uint64_t[r.n ? r.n : 1]);
-    r.c.reset(new (std::nothrow) uint32_t[r.n ? r.n : 1]);
-    if (!r.k || !r.c) return KMC_ENOMEM;
-    if (r.n) {
-      KMC_CUDA_TRY(cudaMemcpyAsync(r.k.get(), as<uint64_t>(e.res_kmers) + a0, r.n * 8, cudaMemcpyDeviceToHost, e.st));
-      KMC_CUDA_TRY(cudaMemcpyAsync(r.c.get(), as<uint32_t>(e.ovals2) + a0, r.n * 4, cudaMemcpyDeviceToHost, e.st));
-    }
+    b->res_off[s] = at + sb[j - s0];
+    b->res_n[s] = sb[j - s0 + 1] - sb[j - s0];
   }
-  KMC_CUDA_TRY(cudaStreamSynchronize(e.st));
+  b->aused += n_sv;
   b->stats.n_kmers_out += n_sv;
   return KMC_OK;
 }
@@ -733,8 +763,9 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
     for (uint64_t r = 0; r < n_reads[s]; ++r)
       if (offsets[s][r + 1] < offsets[s][r]) return KMC_EINPUT;
   }
-  b->res.clear();
-  b->res.resize(n_sets);
+  b->res_off.assign(n_sets, 0);
+  b->res_n.assign(n_sets, 0);
+  b->aused = 0;
   b->stats = kmc_batch_stats{};
   const auto t_start = std::chrono::steady_clock::now();
   // sets grouped by k; large sets go through the single-set path
@@ -826,13 +857,12 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
     if (!rc) rc = kmc_count(hh);
     uint64_t n = 0;
     if (!rc) rc = kmc_result_size(hh, &n);
+    if (!rc) rc = arena_reserve(b, n);
     if (!rc) {
-      BatchSetResult &r = b->res[s];
-      r.n = n;
-      r.k.reset(new (std::nothrow) uint64_t[n ? n : 1]);
-      r.c.reset(new (std::nothrow) uint32_t[n ? n : 1]);
-      if (!r.k || !r.c) rc = KMC_ENOMEM;
-      else rc = kmc_result(hh, r.k.get(), r.c.get(), n, &n);
+      b->res_off[s] = b->aused;
+      b->res_n[s] = n;
+      rc = kmc_result(hh, b->ak + b->aused, b->ac + b->aused, n, &n);
+      b->aused += n;
     }
     if (rc) {  // a failed handle is not reused
       kmc_close(hh);
@@ -848,10 +878,10 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
 
 int kmc_batch_result(kmc_batch *b, uint32_t set, const uint64_t **kmers, const uint32_t **counts,
                      uint64_t *n) {
-  if (!b || set >= b->res.size()) return KMC_EINVAL;
-  if (kmers) *kmers = b->res[set].k.get();
-  if (counts) *counts = b->res[set].c.get();
-  if (n) *n = b->res[set].n;
+  if (!b || set >= b->res_n.size()) return KMC_EINVAL;
+  if (kmers) *kmers = b->ak ? b->ak + b->res_off[set] : nullptr;
+  if (counts) *counts = b->ac ? b->ac + b->res_off[set] : nullptr;
+  if (n) *n = b->res_n[set];
   return KMC_OK;
 }
 
@@ -859,9 +889,16 @@ int kmc_batch_result(kmc_batch *b, uint32_t set, const uint64_t **kmers, const u
 
 namespace kmc {
 int batch_take_result(kmc_batch *b, uint32_t set, BatchSetResult *out) {
-  if (!b || set >= b->res.size()) return KMC_EINVAL;
-  *out = std::move(b->res[set]);
-  b->res[set] = BatchSetResult{};
+  if (!b || set >= b->res_n.size()) return KMC_EINVAL;
+  const uint64_t n = b->res_n[set], o = b->res_off[set];
+  out->n = n;
+  out->k.reset(new (std::nothrow) uint64_t[n ? n : 1]);
+  out->c.reset(new (std::nothrow) uint32_t[n ? n : 1]);
+  if (!out->k || !out->c) return KMC_ENOMEM;
+  if (n) {
+    memcpy(out->k.get(), b->ak + o, n * 8);
+    memcpy(out->c.get(), b->ac + o, n * 4);
+  }
   return KMC_OK;
 }
 }  // namespace kmc
@@ -880,6 +917,8 @@ void kmc_batch_close(kmc_batch *b) {
   b->engines.clear();
   for (auto &kv : b->single) kmc_close(kv.second);
   b->single.clear();
+  if (b->ak) cudaFreeHost(b->ak);
+  if (b->ac) cudaFreeHost(b->ac);
   if (b->own_stream) cudaStreamDestroy(b->st);
   delete b;
 }
