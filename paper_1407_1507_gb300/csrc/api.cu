@@ -229,6 +229,21 @@ void release_all(Handle &h) {
   h.ds.copy_st = nullptr;
 }
 
+// Returns the handle's device buffers that scale with the input to the
+// stream-ordered pool (where any handle of the device can reuse them), keeping
+// the small ones and the pinned host staging buffers.  The reads and the
+// result are dropped: the handle is as after kmc_reset.
+void trim_device(Handle &h) {
+  for (Piece *pc : h.pieces) free_piece(pc, h.st);
+  h.pieces.clear();
+  DevBuf *bufs[] = {&h.out_kmers, &h.out_counts, &h.ds.packed, &h.ds.inval, &h.ds.starts, &h.ds.list,
+                    &h.ds.stage_dev[0], &h.ds.stage_dev[1], &h.ds.offs_dev[0], &h.ds.offs_dev[1],
+                    &h.ss.keys, &h.ss.keys_gen, &h.ss.sorted_keys, &h.ss.big_scratch, &h.ss.sv_keys,
+                    &h.ss.sv_counts, &h.ss.acc_keys, &h.ss.acc_counts, &h.ss.o_big_k, &h.ss.o_big_v,
+                    &h.ds.fq_raw, &h.ds.fq_bases, &h.ds.fq_offsets};
+  for (DevBuf *b : bufs) dev_release(*b, h.st);
+}
+
 int validate(const kmc_params *p) {
   if (!p) return KMC_EINVAL;
   if (p->k < 1 || p->k > KMC_MAX_K) return KMC_EINVAL;
@@ -743,6 +758,20 @@ int kmc_reset(kmc_handle *kh) {
   if (!h.map_user) h.map_ready = false;
   return KMC_OK;
 }
+
+}  // extern "C"
+
+namespace kmc {
+int handle_trim(kmc_handle *kh) {
+  if (!kh) return KMC_EINVAL;
+  DeviceGuard g(kh->h.p.device);
+  const int rc = kmc_reset(kh);
+  trim_device(kh->h);
+  return rc;
+}
+}  // namespace kmc
+
+extern "C" {
 
 void kmc_close(kmc_handle *kh) {
   if (!kh) return;

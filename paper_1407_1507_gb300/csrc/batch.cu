@@ -869,6 +869,10 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
       b->single.erase(k[s]);
       return rc;
     }
+    // its sort buffers go back to the pool between large sets (the handle
+    // keeps its pinned staging and stream-ordered state)
+    rc = handle_trim(hh);
+    if (rc) return rc;
     b->stats.n_kmers_out += n;
     b->stats.n_single += 1;
   }

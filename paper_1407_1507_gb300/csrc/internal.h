@@ -214,7 +214,10 @@ struct BatchSetResult {
   std::unique_ptr<uint32_t[]> c;
   uint64_t n = 0;
 };
-// Moves set `set`'s result out of the batch handle (the handle keeps an empty one).
+// kmc_reset, and the handle's input-sized device buffers go back to the
+// stream-ordered pool (for handles kept open between large jobs).
+int handle_trim(kmc_handle *kh);
+// Copies set `set`'s result out of the batch handle.
 int batch_take_result(kmc_batch *b, uint32_t set, BatchSetResult *out);
 
 int sort_pairs_u64(Handle &h, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits);
