@@ -193,7 +193,8 @@ void free_piece(Piece *pc, cudaStream_t st) {
 void release_all(Handle &h) {
   for (Piece *pc : h.pieces) free_piece(pc, h.st);
   h.pieces.clear();
-  DevBuf *bufs[] = {&h.err, &h.map, &h.out_kmers, &h.out_counts, &h.ds.packed, &h.ds.inval,
+  h.ds.abm_ready = false;
+  DevBuf *bufs[] = {&h.err, &h.map, &h.ds.abm, &h.out_kmers, &h.out_counts, &h.ds.packed, &h.ds.inval,
                     &h.ds.starts, &h.ds.list, &h.ds.counters, &h.ds.hist, &h.ds.scan_tmp,
                     &h.ds.bin_scan, &h.ds.stage_dev[0], &h.ds.stage_dev[1], &h.ds.offs_dev[0],
                     &h.ds.offs_dev[1], &h.ss.hist, &h.ss.bucket_base, &h.ss.cursor, &h.ss.flags,

@@ -144,7 +144,7 @@ struct BatchEngine {
   int o_D = 0;
   bool order128 = false;
   // device
-  DevBuf in, offs, set_starts, dyn, err, map;
+  DevBuf in, offs, set_starts, dyn, err, map, abm;
   DevBuf packed, inval, starts, list, hist3, rec_base, word_base, cursors, index, words;
   DevBuf chunk_cnt, chunk_base, chunks, group_D, group_sz, group_base64, group_base, pieces;
   DevBuf hist, bucket_base, flags, fscan, tfirst, tdesc, scan_tmp, keys, sv_keys, sv_counts, sv_slots,
@@ -165,7 +165,7 @@ struct BatchEngine {
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
-    DevBuf *bufs[] = {&in, &offs, &set_starts, &dyn, &err, &map, &packed, &inval, &starts, &list,
+    DevBuf *bufs[] = {&in, &offs, &set_starts, &dyn, &err, &map, &abm, &packed, &inval, &starts, &list,
                       &hist3, &rec_base, &word_base, &cursors, &index, &words, &chunk_cnt,
                       &chunk_base, &chunks, &group_D, &group_sz, &group_base64, &group_base,
                       &pieces, &hist, &bucket_base, &flags, &fscan, &tfirst, &tdesc, &scan_tmp, &keys,
@@ -209,6 +209,7 @@ struct BatchEngine {
     auto E = [&](DevBuf &b, size_t bytes) { return dev_ensure(b, bytes, st); };
     if (E(in, cap_bases + 64) || E(offs, (cap_reads + 2) * 8) || E(set_starts, (max_sets + 2) * 8) ||
         E(dyn, sizeof(BatchDyn)) || E(err, 64) || E(map, (size_t)n_sig * 4) ||
+        E(abm, (size_t)mmer_bm_words((int)m_used) * 4) ||
         E(packed, 2 * n_mwords * 8) || E(inval, n_mwords * 8) || E(starts, n_mwords * 8) ||
         E(list, list_cap * 8) || E(hist3, (size_t)B_total * 24) || E(rec_base, ((size_t)B_total + 1) * 8) ||
         E(word_base, ((size_t)B_total + 1) * 8) || E(cursors, (size_t)B_total * 16) ||
@@ -239,6 +240,8 @@ struct BatchEngine {
     }
     // kernel attributes and occupancies are set here, outside any capture
     KMC_CUDA_TRY(sig_prepare());
+    KMC_CUDA_TRY(build_mmer_bm(as<uint32_t>(abm), (int)m_used, st));
+    KMC_COUNT_LAUNCH();
     KMC_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)scat_smem_bytes(SIG_SMEM_BINS)));
     KMC_CUDA_TRY(cudaFuncSetAttribute(kx0_scatter_kernel<uint64_t>,
@@ -438,6 +441,7 @@ int BatchEngine::sequence() {
   a.k = k;
   a.m = (int)m_used;
   a.map = as<uint32_t>(map);
+  a.abm = as<uint32_t>(abm);
   a.n_bins = B_total;
   a.list = as<uint64_t>(list);
   a.n_list = &d->n_list;
@@ -616,12 +620,29 @@ int make_engine(kmc_batch *b, uint32_t k, const Tuning &t, std::unique_ptr<Batch
 int run_sub(kmc_batch *b, BatchEngine &e, const uint32_t *idx, uint32_t s0, uint32_t s1,
             const char *const *bases, const uint64_t *const *offsets, const uint64_t *n_reads,
             bool graph, float *ms) {
+  // Reads in page-locked host memory (every set of the sub-batch) are copied
+  // to the device set by set, without the host copy into the staging buffer
+  // (the first sub-batch of an engine still stages them: its bin map is built
+  // from the staged reads).
+  bool direct = e.map_ready;
+  for (uint32_t j = s0; j < s1 && direct; ++j) {
+    const uint32_t s = idx[j];
+    if (!offsets[s][n_reads[s]]) continue;
+    cudaPointerAttributes at{};
+    direct = cudaPointerGetAttributes(&at, bases[s]) == cudaSuccess && at.type == cudaMemoryTypeHost;
+  }
+  cudaGetLastError();  // a pageable pointer may leave an error behind on some drivers
   uint64_t pos = 0, rd = 0;
   for (uint32_t j = s0; j < s1; ++j) {
     const uint32_t s = idx[j];
     const uint64_t nb = offsets[s][n_reads[s]];
     e.h_set_starts[j - s0] = pos;
-    memcpy(e.h_in + pos, bases[s], nb);
+    if (direct) {
+      if (nb)
+        KMC_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(e.in.p) + pos, bases[s], nb, cudaMemcpyHostToDevice, e.st));
+    } else {
+      memcpy(e.h_in + pos, bases[s], nb);
+    }
     for (uint64_t r = 0; r < n_reads[s]; ++r) e.h_offs[rd + r] = pos + offsets[s][r];
     pos += nb;
     rd += n_reads[s];
@@ -633,7 +654,7 @@ int run_sub(kmc_batch *b, BatchEngine &e, const uint32_t *idx, uint32_t s0, uint
   e.h_dyn->n_stream = n_stream;
   e.h_dyn->n_reads = rd;
   e.h_dyn->n_sets = s1 - s0;
-  KMC_CUDA_TRY(cudaMemcpyAsync(e.in.p, e.h_in, n_stream, cudaMemcpyHostToDevice, e.st));
+  if (!direct) KMC_CUDA_TRY(cudaMemcpyAsync(e.in.p, e.h_in, n_stream, cudaMemcpyHostToDevice, e.st));
   KMC_CUDA_TRY(cudaMemcpyAsync(e.offs.p, e.h_offs, (rd + 1) * 8, cudaMemcpyHostToDevice, e.st));
   KMC_CUDA_TRY(cudaMemcpyAsync(e.set_starts.p, e.h_set_starts, (e.max_sets + 1) * 8, cudaMemcpyHostToDevice, e.st));
   KMC_CUDA_TRY(cudaMemcpyAsync(e.dyn.p, e.h_dyn, sizeof(BatchDyn), cudaMemcpyHostToDevice, e.st));

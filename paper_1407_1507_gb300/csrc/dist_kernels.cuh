@@ -145,6 +145,7 @@ struct SigArgs {
   uint32_t n_slots;                // 0 or 1: a single set
   uint32_t bins_per_slot;
   uint32_t no_filter;              // 1: canonical minimizers (no Sect. 2.2 filter)
+  const uint32_t *abm;             // allowed m-mers of length m, one bit each (lane-block scan)
 };
 
 // Set holding stream position pos (largest s with set_starts[s] <= pos).
@@ -367,6 +368,30 @@ __global__ void __launch_bounds__(SIG_THREADS) sig_kernel(SigArgs a) {
   }
 }
 
+// The Sect. 2.2 rule as one bit per m-mer (4^m / 32 words), built on the
+// device once per handle or batch engine: the lane-block scan looks a
+// canonical m-mer up instead of testing its AAA / ACA / AA patterns.
+inline uint32_t mmer_bm_words(int m) { return ((1u << (2 * m)) + 31u) / 32u; }
+__global__ void mmer_bm_kernel(uint32_t *bm, int m, uint32_t n_words) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += gridDim.x * blockDim.x) {
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t v = w * 32u + (uint32_t)b;
+      if (v < (1u << (2 * m)) && mmer_allowed(v, m)) bits |= 1u << b;
+    }
+    bm[w] = bits;
+  }
+}
+// Launches the build on `st` (bm holds mmer_bm_words(m) words); 1 launch.
+inline cudaError_t build_mmer_bm(uint32_t *bm, int m, cudaStream_t st) {
+  const uint32_t n = mmer_bm_words(m);
+  mmer_bm_kernel<<<(n + 255) / 256, 256, 0, st>>>(bm, m, n);
+  return cudaGetLastError();
+}
+__device__ __forceinline__ bool mmer_bit(const uint32_t *bm, uint32_t v) {
+  return (__ldg(bm + (v >> 5)) >> (v & 31u)) & 1u;
+}
+
 // ----------------------------------------------- a2, lane-block version
 // Same result as sig_kernel, organised for fewer instructions per position.
 // Each of the 256 lanes of a CTA owns a block of w = k-m+1 consecutive
@@ -505,6 +530,7 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
   // 2-bit codes stream out of a register word, refilled every 32 bases
   const int64_t p0 = B0 + (int64_t)L * w;               // >= B0 >= LB, LBm
   {
+    const uint32_t *abm = a.abm;  // allowed m-mers (Sect. 2.2)
     const uint32_t mmask = SENT - 1u;
     const uint32_t bit0 = (uint32_t)(2 * (p0 - LB));
     int wi = (int)(bit0 >> 6);
@@ -529,7 +555,7 @@ __global__ void __launch_bounds__(SIG2_LANES) sig2_kernel(SigArgs a) {
       fw = ((fw << 2) | c) & mmask;
       rc = (rc >> 2) | ((3u - c) << rsh);
       const uint32_t cn = fw < rc ? fw : rc;                 // canonical m-mer (Sect. 2.1)
-      const uint32_t v = (NOFILTER || mmer_allowed(cn, m)) ? cn : SENT;  // Sect. 2.2 filter
+      const uint32_t v = (NOFILTER || mmer_bit(abm, cn)) ? cn : SENT;  // Sect. 2.2 filter
       V[L * stride + j] = (VT)v;
       pm = v < pm ? v : pm;
       P[L * stride + j] = (VT)pm;

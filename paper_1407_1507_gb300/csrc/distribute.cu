@@ -76,6 +76,7 @@ SigArgs sig_args(Handle &h, const StreamInfo &si, const uint64_t *d_offsets, uin
   a.map = as<uint32_t>(h.map);
   a.n_bins = h.p.n_bins;
   a.err = as<uint32_t>(h.err);
+  a.abm = h.ds.abm_ready ? as<uint32_t>(h.ds.abm) : nullptr;
   a.n_stream_dyn = nullptr;
   a.n_reads_dyn = nullptr;
   a.set_starts = nullptr;
@@ -84,9 +85,17 @@ SigArgs sig_args(Handle &h, const StreamInfo &si, const uint64_t *d_offsets, uin
   return a;
 }
 
-int launch_sig(Handle &h, const SigArgs &a, uint64_t n_stream, int stage) {
+int launch_sig(Handle &h, const SigArgs &a0, uint64_t n_stream, int stage) {
   KMC_CUDA_TRY(sig_prepare());
   if (n_stream == 0) return KMC_OK;
+  SigArgs a = a0;
+  if (!h.ds.abm_ready) {
+    if (dev_ensure(h.ds.abm, (size_t)mmer_bm_words(a.m) * 4, h.st)) return KMC_ENOMEM;
+    KMC_CUDA_TRY(build_mmer_bm(as<uint32_t>(h.ds.abm), a.m, h.st));
+    KMC_COUNT_LAUNCH();
+    h.ds.abm_ready = true;
+  }
+  a.abm = as<uint32_t>(h.ds.abm);
   StageScope sc(h, stage);
   if (sig_launch(a, n_stream, (h.p.debug_flags & KMC_DEBUG_SIG_TILE) != 0, h.st)) KMC_COUNT_LAUNCH();
   KMC_CUDA_TRY(cudaGetLastError());

@@ -88,6 +88,8 @@ struct Piece {
 // Per-call scratch of the distribution phase (reused).
 struct DistScratch {
   DevBuf packed, inval, starts;  // bit streams of the current piece
+  DevBuf abm;                    // allowed m-mers (Sect. 2.2), one bit each, built once
+  bool abm_ready = false;
   DevBuf list;                   // uint64 super k-mer list
   DevBuf counters;               // device counters
   DevBuf hist;                   // per-bin histograms (records, words, kmers)
