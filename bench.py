@@ -483,8 +483,11 @@ def run_batched(args, local_rank):
 
         po = PinnedOut()
 
+        stage_sum = {}
+
         def plain_pass():
             out, busy = [], 0.0
+            stage_sum.clear()
             for w in sets:
                 h = handles[w.k]
                 t = time.perf_counter()
@@ -494,10 +497,13 @@ def run_batched(args, local_rank):
                 res = po.get(kmc, h, w.k)
                 busy += time.perf_counter() - t
                 out.append(digest(*res))  # outside the timed part
+                for x, v in kmc.kmc_stats_get(h)["ms_stage"].items():
+                    stage_sum[x] = stage_sum.get(x, 0.0) + v
             return out, busy
 
         plain_pass()
         plain, t_plain = plain_pass()
+        log("batched: plain stage ms " + json.dumps({x: round(v, 1) for x, v in stage_sum.items() if v}))
         log(f"batched: plain pass {t_plain:.2f} s")
     finally:
         for h in handles.values():
@@ -536,6 +542,7 @@ def run_batched(args, local_rank):
             "kmer_positions": pos, "bases": bases, "generation_s": round(gen_s, 2),
             "plain_s": round(t_plain, 4), "batched_s": round(t_batch, 4),
             "plain_kmers_per_s": pos / t_plain, "batched_kmers_per_s": pos / t_batch,
+            "plain_device_stage_ms": {x: round(v, 1) for x, v in stage_sum.items() if v},
             "speedup": t_plain / t_batch, "identical_to_plain": bool(same),
             "plain": "one open handle per k, reset per set, page-locked host input, result read back into "
                      "reused pinned buffers; time of those calls only",

@@ -339,7 +339,9 @@ int kmc_debug_bin_keys(kmc_handle *h, uint32_t bin, uint64_t *keys, uint64_t cap
  * sequence of a sub-batch reads every data-dependent size from device memory,
  * so it runs without host synchronisation: it is captured once as a CUDA
  * graph and replayed for every sub-batch of the same k.  A set larger than
- * the capacity is counted by the single-set path.  With KMC_BATCH_AUTOTUNE
+ * the capacity, or of 4 MiB of bases or more, is counted by the single-set
+ * path instead, two such sets at a time on streams of their own (the batch
+ * pays for itself while per-set launches and host steps dominate).  With KMC_BATCH_AUTOTUNE
  * the first sub-batch of each k times a few settings (bins per set, bucket
  * width, tile size) and the fastest is kept for the handle's lifetime.
  *

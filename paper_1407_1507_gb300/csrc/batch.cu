@@ -17,6 +17,10 @@
 #include <map>
 #include <memory>
 #include <vector>
+#include <atomic>
+#include <mutex>
+#include <shared_mutex>
+#include <thread>
 
 #include "internal.h"
 #include "sortlib.cuh"
@@ -550,6 +554,17 @@ int BatchEngine::sequence() {
 
 using namespace kmc;
 
+namespace kmc {
+namespace {
+// Sets of at least this many bases are counted one at a time on the
+// single-set path (measured: the batch engine, which builds every key twice,
+// pays for itself only while per-set launch and host steps dominate, i.e.
+// for sets of a few MB), by this many host threads (lanes) at once.
+constexpr uint64_t kSingleMinBases = 4ull << 20;
+constexpr int kSingleLanes = 2;
+}  // namespace
+}  // namespace kmc
+
 struct kmc_batch {
   kmc_params base{};
   uint64_t cap_bases = 0, cap_reads = 0;
@@ -567,8 +582,11 @@ struct kmc_batch {
   uint32_t *ac = nullptr;
   uint64_t acap = 0, aused = 0;
   std::vector<uint64_t> res_off, res_n;
-  // sets above the capacity: one handle per k, kept open and reset per set
-  std::map<uint32_t, kmc_handle *> single;
+  // sets counted one at a time: per lane, one handle per k, kept open and
+  // reset per set
+  std::map<uint32_t, kmc_handle *> single[kSingleLanes];
+  std::mutex single_mu;
+  std::shared_mutex arena_mu;  // growth (exclusive) against copies into the arena (shared)
   kmc_batch_stats stats{};
 };
 
@@ -794,7 +812,7 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
   std::vector<uint32_t> single;
   for (uint32_t s = 0; s < n_sets; ++s) {
     const uint64_t nb = offsets[s][n_reads[s]];
-    if (nb + 64 > b->cap_bases || n_reads[s] + 1 > b->cap_reads) single.push_back(s);
+    if (nb + 64 > b->cap_bases || n_reads[s] + 1 > b->cap_reads || nb >= kSingleMinBases) single.push_back(s);
     else by_k[k[s]].push_back(s);
   }
   const bool graph = !(b->flags & KMC_BATCH_NO_GRAPH);
@@ -858,44 +876,76 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
     b->stats.tile_keys = 256 * t.ipt;
     b->stats.bucket_keys = 256 * t.ipt / t.bucket_div;
   }
-  for (uint32_t s : single) {
-    kmc_handle *&hh = b->single[k[s]];
-    int rc = KMC_OK;
-    if (!hh) {
-      kmc_params sp = b->base;
-      sp.k = k[s];
-      sp.cuda_stream = b->st;
-      sp.x = 0;
-      rc = kmc_open(&hh, &sp);
-      if (rc) {
-        b->single.erase(k[s]);
-        return rc;
+  // Sets counted one at a time on open handles (a handle per k and lane, each
+  // on its own stream): kSingleLanes host threads take them in turn, so that
+  // one set's host steps overlap another's kernels.
+  std::atomic<uint32_t> next{0};
+  std::atomic<int> first_err{KMC_OK};
+  std::atomic<uint64_t> kmers_out{0};
+  auto lane = [&](int li) {
+    for (;;) {
+      const uint32_t q = next.fetch_add(1);
+      if (q >= single.size() || first_err.load() != KMC_OK) return;
+      const uint32_t s = single[q];
+      kmc_handle *hh = nullptr;
+      {
+        std::lock_guard<std::mutex> g(b->single_mu);
+        hh = b->single[li][k[s]];
       }
-    } else {
-      rc = kmc_reset(hh);
+      int rc = KMC_OK;
+      if (!hh) {
+        kmc_params sp = b->base;
+        sp.k = k[s];
+        sp.cuda_stream = nullptr;  // a stream of its own
+        sp.x = 0;
+        rc = kmc_open(&hh, &sp);
+        if (rc) {
+          first_err.store(rc);
+          return;
+        }
+        std::lock_guard<std::mutex> g(b->single_mu);
+        b->single[li][k[s]] = hh;
+      } else {
+        rc = kmc_reset(hh);
+      }
+      if (!rc) rc = kmc_add_reads(hh, bases[s], offsets[s], n_reads[s]);
+      if (!rc) rc = kmc_count(hh);
+      uint64_t n = 0, off = 0;
+      if (!rc) rc = kmc_result_size(hh, &n);
+      if (!rc) {  // room in the arena (growing it waits for the copies into it)
+        std::unique_lock<std::shared_mutex> g(b->arena_mu);
+        rc = arena_reserve(b, n);
+        off = b->aused;
+        b->aused += rc ? 0 : n;
+      }
+      if (!rc) {
+        std::shared_lock<std::shared_mutex> g(b->arena_mu);
+        b->res_off[s] = off;
+        b->res_n[s] = n;
+        rc = kmc_result(hh, b->ak + off, b->ac + off, n, &n);
+      }
+      // its sort buffers go back to the pool between large sets (the handle
+      // keeps its pinned staging and stream-ordered state)
+      if (!rc) rc = handle_trim(hh);
+      if (rc) {  // a failed handle is not reused
+        kmc_close(hh);
+        std::lock_guard<std::mutex> g(b->single_mu);
+        b->single[li].erase(k[s]);
+        first_err.store(rc);
+        return;
+      }
+      kmers_out += n;
     }
-    if (!rc) rc = kmc_add_reads(hh, bases[s], offsets[s], n_reads[s]);
-    if (!rc) rc = kmc_count(hh);
-    uint64_t n = 0;
-    if (!rc) rc = kmc_result_size(hh, &n);
-    if (!rc) rc = arena_reserve(b, n);
-    if (!rc) {
-      b->res_off[s] = b->aused;
-      b->res_n[s] = n;
-      rc = kmc_result(hh, b->ak + b->aused, b->ac + b->aused, n, &n);
-      b->aused += n;
-    }
-    if (rc) {  // a failed handle is not reused
-      kmc_close(hh);
-      b->single.erase(k[s]);
-      return rc;
-    }
-    // its sort buffers go back to the pool between large sets (the handle
-    // keeps its pinned staging and stream-ordered state)
-    rc = handle_trim(hh);
-    if (rc) return rc;
-    b->stats.n_kmers_out += n;
-    b->stats.n_single += 1;
+  };
+  if (!single.empty()) {
+    const int n_lanes = (int)std::min<size_t>(kSingleLanes, single.size());
+    std::vector<std::thread> th;
+    for (int li = 1; li < n_lanes; ++li) th.emplace_back(lane, li);
+    lane(0);
+    for (std::thread &t : th) t.join();
+    if (first_err.load() != KMC_OK) return first_err.load();
+    b->stats.n_kmers_out += kmers_out.load();
+    b->stats.n_single += (uint32_t)single.size();
   }
   b->stats.ms_wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return KMC_OK;
@@ -940,8 +990,10 @@ void kmc_batch_close(kmc_batch *b) {
   if (!b) return;
   cudaSetDevice(b->base.device);
   b->engines.clear();
-  for (auto &kv : b->single) kmc_close(kv.second);
-  b->single.clear();
+  for (auto &m : b->single) {
+    for (auto &kv : m) kmc_close(kv.second);
+    m.clear();
+  }
   if (b->ak) cudaFreeHost(b->ak);
   if (b->ac) cudaFreeHost(b->ac);
   if (b->own_stream) cudaStreamDestroy(b->st);

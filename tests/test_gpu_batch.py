@@ -62,3 +62,30 @@ def test_batch_large_sets_take_single_path_and_ci1():
         _check(b, sets, 1)
     finally:
         kmc.kmc_batch_close(b)
+
+
+def test_batch_sets_of_several_mb_run_in_two_lanes():
+    # sets of 4 MiB of bases or more are counted on the single-set path, two
+    # at a time on their own streams, between small sets that are batched;
+    # page-locked and pageable input mixed; results written into the pinned
+    # arena from both lanes (with a growth in between)
+    rng = random.Random(21)
+    sets = []
+    for i in range(9):
+        g = synth.genome_markov3(rng.randint(200_000, 2_000_000), 5000 + i)
+        nr = 40_000 if i % 3 == 0 else rng.randint(100, 3000)
+        b_, o_ = synth.reads(g, np.full(nr, 150), 0.01, 0.001, 6000 + i)
+        sets.append((b_, o_, rng.choice([21, 28, 31])))
+    torch = pytest.importorskip("torch")
+    pinned = torch.from_numpy(sets[3][0]).pin_memory().numpy()
+    sets[3] = (pinned, sets[3][1], sets[3][2])
+    p = kmc.make_params(28, m=7, n_bins=64)
+    b = kmc.kmc_batch_open(p, 64 << 20, 500_000, 32, 0)
+    try:
+        for _ in range(2):
+            kmc.kmc_batch_run(b, [(x[0], x[1]) for x in sets], [x[2] for x in sets])
+            st = kmc.kmc_batch_stats_get(b)
+            assert st["n_single"] == 3
+            _check(b, sets, 2)
+    finally:
+        kmc.kmc_batch_close(b)
