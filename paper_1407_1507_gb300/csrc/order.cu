@@ -15,7 +15,7 @@ namespace {
 constexpr int PAIR_THREADS = 256;
 constexpr int PAIR_IPT = 8;   // tile = 2048 pairs (three CTAs per SM)
 constexpr int PAIR_BIG_IPT = 8;
-constexpr int PAIR_MAX_D = 25;  // large lists: small buckets even under skewed top digits
+constexpr int PAIR_MAX_D = 22;
 
 template <typename K>
 __global__ void pair_hist_kernel(const K *__restrict__ keys, uint64_t n, int key_bits, int D,
