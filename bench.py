@@ -222,7 +222,20 @@ def _cpu_model():
 # ncu capture of the 1 M-read case of the mid workload (the kernels' traffic
 # grows with the keys, so it is scaled by this run's positions); filled in for
 # the stages whose kernels were captured after their last change.
-STAGE_DRAM_BYTES_PER_KEY = {}
+# kx_scatter: the upper sweep (every key) and the lower sweep (keys of the bins
+# that are not counted straight from their super buckets), captured separately:
+# 1,863.8 MB for 119,586,137 keys (upper, 512 bins) and 2,808.7 MB for the same
+# keys all in the lower sweep (8 bins: its histogram pass reads the super
+# buckets once more where they outgrow L2).  tile_sort: 992.2 MB (super-bucket
+# count, 512 bins) and 992.8 MB (tile count, 8 bins) for the same keys.
+STAGE_DRAM_BYTES_PER_KEY = {
+    "kx_scatter": (1863.8e6 / 119586137, 2808.7e6 / 119586137),
+    "tile_sort": (992.2e6 / 119586137, 992.8e6 / 119586137),
+}
+# Signature scan: warp instructions per base of a piece (ncu sm__inst_executed
+# of one piece's launch: 552.0 M for 150 M bases), against the issue peak of
+# 4 warp instructions per SM and clock.
+SIG_WARP_INST_PER_BASE = 552.0e6 / 150e6
 
 
 def stage_bytes(st, k):
@@ -316,7 +329,15 @@ def run_ours(args, rank, local_rank, world):
     achieved = stages[dom]["gbs"]
     traffic = None
     if dom in STAGE_DRAM_BYTES_PER_KEY and k <= 32 and st0.get("x_used", 0) == 0:
-        traffic = int(STAGE_DRAM_BYTES_PER_KEY[dom] * st0["n_kmer_positions"])
+        fused = st0.get("n_fused_keys", 0)
+        a, b = STAGE_DRAM_BYTES_PER_KEY[dom]
+        traffic = int(a * (st0["n_kmer_positions"] if dom == "kx_scatter" else fused)
+                      + b * (st0["n_kmer_positions"] - fused))
+    if "signature" in stages and clk.get("sm_mhz"):
+        peak_inst = 4 * torch.cuda.get_device_properties(dev).multi_processor_count * clk["sm_mhz"] * 1e6
+        got_inst = SIG_WARP_INST_PER_BASE * st0["n_bases"] / (stages["signature"]["ms"] / 1e3)
+        stages["signature"]["alu_frac"] = round(got_inst / peak_inst, 4)
+        stages["signature"]["alu_bound"] = "warp-instruction issue (4 per SM and clock)"
     roofline = {"bound": "hbm", "kernel_stage": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
