@@ -585,6 +585,10 @@ struct kmc_batch {
   // sets counted one at a time: per lane, one handle per k, kept open and
   // reset per set
   std::map<uint32_t, kmc_handle *> single[kSingleLanes];
+  // the bin map each of those handles built from its first set, reused for the
+  // sets after it (the result does not depend on the map; this saves the
+  // sample scan per set, as the batch engine's one map per k does)
+  std::map<uint32_t, std::vector<uint32_t>> single_map[kSingleLanes];
   std::mutex single_mu;
   std::shared_mutex arena_mu;  // growth (exclusive) against copies into the arena (shared)
   kmc_batch_stats stats{};
@@ -888,9 +892,11 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
       if (q >= single.size() || first_err.load() != KMC_OK) return;
       const uint32_t s = single[q];
       kmc_handle *hh = nullptr;
+      std::vector<uint32_t> *map = nullptr;
       {
         std::lock_guard<std::mutex> g(b->single_mu);
         hh = b->single[li][k[s]];
+        map = &b->single_map[li][k[s]];
       }
       int rc = KMC_OK;
       if (!hh) {
@@ -907,8 +913,15 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
         b->single[li][k[s]] = hh;
       } else {
         rc = kmc_reset(hh);
+        // once set, the map stays with the handle across resets
+        if (!rc && !map->empty() && !hh->h.map_user) rc = kmc_set_bin_map(hh, map->data(), map->size());
       }
       if (!rc) rc = kmc_add_reads(hh, bases[s], offsets[s], n_reads[s]);
+      if (!rc && map->empty()) {
+        map->resize(hh->h.n_sig);
+        rc = kmc_get_bin_map(hh, map->data(), map->size());
+        if (rc) map->clear();
+      }
       if (!rc) rc = kmc_count(hh);
       uint64_t n = 0, off = 0;
       if (!rc) rc = kmc_result_size(hh, &n);
@@ -931,6 +944,7 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
         kmc_close(hh);
         std::lock_guard<std::mutex> g(b->single_mu);
         b->single[li].erase(k[s]);
+        b->single_map[li].erase(k[s]);
         first_err.store(rc);
         return;
       }

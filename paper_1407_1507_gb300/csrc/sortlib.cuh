@@ -1001,9 +1001,18 @@ tile_hash_kernel(const uint64_t *__restrict__ keys, TilePlan plan, uint32_t *wor
 // the keys whose multiplicative hash selects p, so all copies of a key fall
 // in one pass), re-reading it, mostly from L2; a pass that overflows is split
 // in two without recounting the passes already emitted.
+#ifndef KMC_SUPER_SLOTS
+#define KMC_SUPER_SLOTS 8192
+#endif
+#ifndef KMC_SUPER_UNROLL
+#define KMC_SUPER_UNROLL 4
+#endif
+#ifndef KMC_SUPER_MINB
+#define KMC_SUPER_MINB 2
+#endif
 constexpr int SUPER_THREADS = 512;
-constexpr int SUPER_SLOTS = 8192;
-constexpr int SUPER_UNROLL = 4;
+constexpr int SUPER_SLOTS = KMC_SUPER_SLOTS;
+constexpr int SUPER_UNROLL = KMC_SUPER_UNROLL;
 constexpr int SUPER_BATCH = SUPER_THREADS * SUPER_UNROLL;
 constexpr int SUPER_LIMIT = SUPER_SLOTS - 1 - SUPER_BATCH;
 constexpr uint32_t SUPER_MAX_PASSES = 1u << 16;
@@ -1031,7 +1040,7 @@ __device__ __forceinline__ uint32_t super_pass_of(uint64_t key, int lg) {
 }
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, KMC_SUPER_MINB)
 super_hash_kernel(SuperArgs a, CountOut<uint64_t> out, uint32_t *err) {
   constexpr int SPT = SUPER_SLOTS / THREADS;
   static_assert(THREADS == SUPER_THREADS && SUPER_SLOTS % THREADS == 0 && SPT <= 32, "layout");
