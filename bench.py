@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--served-jobs", type=int, default=1000)
     ap.add_argument("--served-scale", type=float, default=0.02,
                     help="request sizes of the served workload (1.0 with 5000 jobs: the full workload)")
+    ap.add_argument("--served-mem-gb", type=float, default=96.0,
+                    help="predicted device memory the served jobs in flight may take")
     ap.add_argument("--served-rho", type=float, nargs="+", default=[0.5, 0.8, 0.95, 1.2],
                     help="loads relative to the serial plain path's capacity")
     ap.add_argument("--cpu-sample-reads", type=int, default=CPU_SAMPLE_READS)
@@ -622,15 +624,17 @@ def run_served(args, local_rank):
     rng = np.random.default_rng(20140715)
     try:
         for rho in args.served_rho:
-            out[f"rho={rho}"] = _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos)
+            out[f"rho={rho}"] = _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos,
+                                            int(args.served_mem_gb * (1 << 30)))
             log(f"served: rho={rho} done")
     finally:
         host_unregister(pinned)
     out["input"] = "page-locked host memory (the read pools registered once), zero-copy submission"
+    out["mem_budget_gb"] = args.served_mem_gb
     return out
 
 
-def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
+def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos, mem_budget):
     lam = rho / float(np.mean(svc))
     arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
     arrivals -= arrivals[0]
@@ -639,10 +643,10 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos):
         done = max(a, done) + sv
         lat_serial.append((done - a) * 1e3)
     serial_wall = done
-    # predicted device bytes in flight: up to 96 GB of the GPU's memory
+    # predicted device bytes in flight (32 per input byte): mem_budget of the GPU's memory
     s = kmc.kmc_server_open(kmc.make_params(28, m=7, n_bins=64, device=local_rank),
                             batch_bases=128 << 20, batch_reads=1_000_000, batch_sets=256, n_workers=2,
-                            mem_budget=96 << 30, warm_k=(21, 28, 31))
+                            mem_budget=mem_budget, warm_k=(21, 28, 31))
     lat, same = [None] * len(reqs), [False] * len(reqs)
     ids = [None] * len(reqs)
     have = threading.Semaphore(0)
