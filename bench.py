@@ -645,7 +645,7 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos, mem_budget):
     serial_wall = done
     # predicted device bytes in flight (32 per input byte): mem_budget of the GPU's memory
     s = kmc.kmc_server_open(kmc.make_params(28, m=7, n_bins=64, device=local_rank),
-                            batch_bases=128 << 20, batch_reads=1_000_000, batch_sets=256, n_workers=2,
+                            batch_bases=64 << 20, batch_reads=500_000, batch_sets=256, n_workers=4,
                             mem_budget=mem_budget, warm_k=(21, 28, 31))
     lat, same = [None] * len(reqs), [False] * len(reqs)
     ids = [None] * len(reqs)

@@ -384,7 +384,8 @@ void kmc_batch_close(kmc_batch *b);
  * job's host reads and queues it (it never blocks on the GPU).  n_workers
  * worker threads, each with its own CUDA stream and resident batch engines
  * (kmc_batch_*), repeatedly admit queued jobs in arrival order while they
- * fit one batch (batch_bases bytes, batch_reads reads, batch_sets jobs) and
+ * fit one batch (batch_bases bytes, batch_reads reads, batch_sets jobs; a job
+ * of 4 MiB of bases or more, counted on the single-set path, runs alone) and
  * the device-memory budget: the predicted footprint of a job is 32 bytes
  * per input byte, and the jobs in flight never exceed mem_budget (a job is
  * always admitted when nothing is in flight).  Jobs that arrive while

@@ -556,11 +556,8 @@ using namespace kmc;
 
 namespace kmc {
 namespace {
-// Sets of at least this many bases are counted one at a time on the
-// single-set path (measured: the batch engine, which builds every key twice,
-// pays for itself only while per-set launch and host steps dominate, i.e.
-// for sets of a few MB), by this many host threads (lanes) at once.
-constexpr uint64_t kSingleMinBases = 4ull << 20;
+// Sets of kSingleMinBases or more (internal.h) are counted one at a time on
+// the single-set path, by this many host threads (lanes) at once.
 constexpr int kSingleLanes = 2;
 }  // namespace
 }  // namespace kmc

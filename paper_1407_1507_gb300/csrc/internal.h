@@ -210,6 +210,12 @@ int debug_bin_keys(Handle &h, uint32_t bin, uint64_t *keys, uint64_t capacity, u
                    uint32_t *words_per_key);
 
 // order.cu: sort (key, value) pairs in place by key bits [0, key_bits)
+// Read sets of at least this many bases are counted on the single-set path
+// by the batch and server calls (the batch engine builds every key twice and
+// pays for itself only while per-set launches and host steps dominate, i.e.
+// for sets of a few MB).
+constexpr uint64_t kSingleMinBases = 4ull << 20;
+
 // One set's result of a batch run, in host memory.
 struct BatchSetResult {
   std::unique_ptr<uint64_t[]> k;

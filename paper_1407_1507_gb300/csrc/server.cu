@@ -82,7 +82,7 @@ bool fits(const kmc_server &s, const std::vector<Job *> &take, uint64_t nb, uint
   const uint64_t jb = j.n_bases;
   if (s.inflight + fp + j.footprint > c.mem_budget && !(take.empty() && s.inflight == 0)) return false;
   if (take.empty()) return true;  // a job always fits an empty batch (large ones run alone)
-  if (take.size() >= c.batch_sets) return false;
+  if (take.size() >= c.batch_sets || jb >= kSingleMinBases) return false;
   return nb + jb + 64 <= c.batch_bases && nr + j.n_reads + 1 <= c.batch_reads;
 }
 
@@ -140,7 +140,10 @@ void worker(kmc_server *s, int w) {
         nb += j->n_bases;
         nr += j->n_reads;
         fp += j->footprint;
-        if (nb + 64 > s->cfg.batch_bases) break;  // a large job runs alone
+        // a job counted on the single-set path runs alone, so that a worker
+        // comes back for more as soon as it is done (the workers run such
+        // jobs side by side)
+        if (nb + 64 > s->cfg.batch_bases || j->n_bases >= kSingleMinBases) break;
       }
       if (take.empty()) {
         // the head job does not fit the memory budget beside the batches in
