@@ -13,6 +13,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -46,7 +47,61 @@ struct Job {
   uint64_t footprint = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   int status = 0;  // 0 queued, 1 running, 2 done, < 0 error code
-  BatchSetResult res;  // the k-mers and counts, moved out of the batch handle
+  BatchSetResult res;  // the k-mers and counts of a batched job (copied out of the batch)
+  // ... or of a job counted on the single-set path: a pinned buffer of the
+  // server's pool, written by the device and given back at release
+  uint64_t *pk = nullptr;
+  uint32_t *pc = nullptr;
+  uint64_t pcap = 0, pn = 0;
+};
+
+// Page-locked result buffers, recycled between jobs (no allocation and no
+// page faults once the pool has grown to the load).
+struct ResultPool {
+  struct Buf {
+    uint64_t *k;
+    uint32_t *c;
+    uint64_t cap;
+  };
+  std::mutex mu;
+  std::vector<Buf> free;
+  int take(uint64_t n, Buf *out) {
+    {
+      std::lock_guard<std::mutex> g(mu);
+      size_t best = free.size();
+      for (size_t i = 0; i < free.size(); ++i)
+        if (free[i].cap >= n && (best == free.size() || free[i].cap < free[best].cap)) best = i;
+      if (best < free.size()) {
+        *out = free[best];
+        free.erase(free.begin() + (long)best);
+        return KMC_OK;
+      }
+    }
+    const uint64_t cap = std::max<uint64_t>(n + n / 4, 1u << 16);
+    void *k = nullptr, *c = nullptr;
+    if (host_alloc(&k, cap * 8, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return KMC_ENOMEM;
+    }
+    if (host_alloc(&c, cap * 4, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(k);
+      return KMC_ENOMEM;
+    }
+    *out = Buf{static_cast<uint64_t *>(k), static_cast<uint32_t *>(c), cap};
+    return KMC_OK;
+  }
+  void give(uint64_t *k, uint32_t *c, uint64_t cap) {
+    if (!k) return;
+    std::lock_guard<std::mutex> g(mu);
+    free.push_back(Buf{k, c, cap});
+  }
+  ~ResultPool() {
+    for (Buf &b : free) {
+      cudaFreeHost(b.k);
+      cudaFreeHost(b.c);
+    }
+  }
 };
 
 }  // namespace
@@ -66,6 +121,11 @@ struct kmc_server {
   bool stop = false;
   std::vector<std::thread> workers;
   std::vector<kmc_batch *> batches;
+  // jobs of kSingleMinBases or more: each worker's own handle per k (own
+  // stream, kept open, its bin map built once), results into the pool
+  std::vector<std::map<uint32_t, kmc_handle *>> singles;
+  std::vector<std::map<uint32_t, std::vector<uint32_t>>> single_maps;
+  ResultPool pool;
   // statistics
   std::vector<double> lat_ms;
   uint64_t done = 0, n_batches = 0, max_batch_jobs = 0, max_inflight_jobs = 0;
@@ -108,6 +168,75 @@ int warm_up(kmc_batch *b, uint64_t mask) {
     if (rc) return rc;
   }
   return KMC_OK;
+}
+
+// A job on the single-set path, counted on the worker's own open handle for
+// its k; the result goes from the device straight into a pooled pinned buffer.
+void run_single(kmc_server *s, int w, Job *j, uint64_t fp) {
+  kmc_handle *&hh = s->singles[w][j->k];
+  std::vector<uint32_t> &map = s->single_maps[w][j->k];
+  int rc = KMC_OK;
+  if (!hh) {
+    kmc_params sp = s->cfg.base;
+    sp.k = j->k;
+    sp.x = 0;
+    sp.cuda_stream = nullptr;
+    rc = kmc_open(&hh, &sp);
+    if (rc) hh = nullptr;
+  } else {
+    rc = kmc_reset(hh);
+    if (!rc && !map.empty() && !hh->h.map_user) rc = kmc_set_bin_map(hh, map.data(), map.size());
+  }
+  if (!rc) rc = kmc_add_reads(hh, j->bp, j->op, j->n_reads);
+  if (!rc && map.empty()) {
+    map.resize(hh->h.n_sig);
+    rc = kmc_get_bin_map(hh, map.data(), map.size());
+    if (rc) map.clear();
+  }
+  if (!rc) rc = kmc_count(hh);
+  uint64_t n = 0;
+  if (!rc) rc = kmc_result_size(hh, &n);
+  ResultPool::Buf buf{nullptr, nullptr, 0};
+  if (!rc) rc = s->pool.take(n, &buf);
+  if (!rc) rc = kmc_result(hh, buf.k, buf.c, n, &n);
+  if (!rc) rc = handle_trim(hh);  // the sort buffers go back to the device pool
+  if (rc && hh) {
+    kmc_close(hh);
+    hh = nullptr;
+    map.clear();
+  }
+  if (rc && buf.k) {
+    s->pool.give(buf.k, buf.c, buf.cap);
+    buf = ResultPool::Buf{nullptr, nullptr, 0};
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    const double t = now_s();
+    j->t_done = t;
+    if (rc == KMC_OK) {
+      j->pk = buf.k;
+      j->pc = buf.c;
+      j->pcap = buf.cap;
+      j->pn = n;
+      j->status = 2;
+      s->lat_ms.push_back((j->t_done - j->t_submit) * 1e3);
+      s->done += 1;
+    } else {
+      j->status = rc;
+      s->error = rc;
+    }
+    std::vector<char>().swap(j->bases);
+    std::vector<uint64_t>().swap(j->offsets);
+    j->bp = nullptr;
+    j->op = nullptr;
+    s->inflight -= fp;
+    s->inflight_jobs -= 1;
+    s->n_batches += 1;
+    s->max_batch_jobs = std::max<uint64_t>(s->max_batch_jobs, 1);
+    s->t_last = t;
+  }
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();
 }
 
 void worker(kmc_server *s, int w) {
@@ -164,6 +293,10 @@ void worker(kmc_server *s, int w) {
         j->status = 1;
         j->t_start = t;
       }
+    }
+    if (take.size() == 1 && take[0]->n_bases >= kSingleMinBases) {
+      run_single(s, w, take[0], fp);
+      continue;
     }
     std::vector<const char *> bp;
     std::vector<const uint64_t *> op;
@@ -247,6 +380,8 @@ int kmc_server_open(kmc_server **out, const kmc_server_cfg *cfg) {
     }
     s->batches.push_back(b);
   }
+  s->singles.resize(c.n_workers);
+  s->single_maps.resize(c.n_workers);
   for (uint32_t w = 0; w < c.n_workers; ++w) s->workers.emplace_back(worker, s, (int)w);
   {
     std::unique_lock<std::mutex> lk(s->mu);
@@ -331,9 +466,9 @@ int kmc_server_result(kmc_server *s, uint64_t job_id, const uint64_t **kmers, co
   Job *j = it->second.get();
   if (j->status < 0) return j->status;
   if (j->status != 2) return KMC_EAGAIN;
-  if (kmers) *kmers = j->res.k.get();
-  if (counts) *counts = j->res.c.get();
-  if (n) *n = j->res.n;
+  if (kmers) *kmers = j->pk ? j->pk : j->res.k.get();
+  if (counts) *counts = j->pk ? j->pc : j->res.c.get();
+  if (n) *n = j->pk ? j->pn : j->res.n;
   if (latency_ms) *latency_ms = (j->t_done - j->t_submit) * 1e3;
   return KMC_OK;
 }
@@ -344,6 +479,7 @@ int kmc_server_release(kmc_server *s, uint64_t job_id) {
   auto it = s->jobs.find(job_id);
   if (it == s->jobs.end()) return KMC_EINVAL;
   if (it->second->status < 2 && it->second->status >= 0) return KMC_ESTATE;
+  s->pool.give(it->second->pk, it->second->pc, it->second->pcap);
   s->jobs.erase(it);
   return KMC_OK;
 }
@@ -399,6 +535,9 @@ void kmc_server_close(kmc_server *s) {
   s->cv_work.notify_all();
   for (std::thread &t : s->workers) t.join();
   for (kmc_batch *b : s->batches) kmc_batch_close(b);
+  for (auto &m : s->singles)
+    for (auto &kv : m) kmc_close(kv.second);
+  for (auto &kv : s->jobs) s->pool.give(kv.second->pk, kv.second->pc, kv.second->pcap);
   delete s;
 }
 
