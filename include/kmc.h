@@ -385,7 +385,8 @@ void kmc_batch_close(kmc_batch *b);
  * worker threads, each with its own CUDA stream and resident batch engines
  * (kmc_batch_*), repeatedly admit queued jobs in arrival order while they
  * fit one batch (batch_bases bytes, batch_reads reads, batch_sets jobs; a job
- * of 4 MiB of bases or more, counted on the single-set path, runs alone) and
+ * of 4 MiB of bases or more runs alone, on the worker's own single-set handle
+ * for its k, its result written into a recycled page-locked buffer) and
  * the device-memory budget: the predicted footprint of a job is 32 bytes
  * per input byte, and the jobs in flight never exceed mem_budget (a job is
  * always admitted when nothing is in flight).  Jobs that arrive while
