@@ -934,9 +934,9 @@ int kmc_batch_run(kmc_batch *b, uint32_t n_sets, const char *const *bases,
         b->res_n[s] = n;
         rc = kmc_result(hh, b->ak + off, b->ac + off, n, &n);
       }
-      // its sort buffers go back to the pool between large sets (the handle
-      // keeps its pinned staging and stream-ordered state)
-      if (!rc) rc = handle_trim(hh);
+      // after a very large set its sort buffers go back to the pool (the
+      // handle keeps its pinned staging and stream-ordered state)
+      if (!rc && offsets[s][n_reads[s]] >= kTrimMinBases) rc = handle_trim(hh);
       if (rc) {  // a failed handle is not reused
         kmc_close(hh);
         std::lock_guard<std::mutex> g(b->single_mu);

@@ -215,6 +215,10 @@ int debug_bin_keys(Handle &h, uint32_t bin, uint64_t *keys, uint64_t capacity, u
 // pays for itself only while per-set launches and host steps dominate, i.e.
 // for sets of a few MB).
 constexpr uint64_t kSingleMinBases = 4ull << 20;
+// Open single-set handles of the batch and server calls give their
+// input-sized device buffers back to the pool after a set of at least this
+// many bases (smaller sets leave them for the next set).
+constexpr uint64_t kTrimMinBases = 256ull << 20;
 
 // One set's result of a batch run, in host memory.
 struct BatchSetResult {

@@ -199,7 +199,7 @@ void run_single(kmc_server *s, int w, Job *j, uint64_t fp) {
   ResultPool::Buf buf{nullptr, nullptr, 0};
   if (!rc) rc = s->pool.take(n, &buf);
   if (!rc) rc = kmc_result(hh, buf.k, buf.c, n, &n);
-  if (!rc) rc = handle_trim(hh);  // the sort buffers go back to the device pool
+  if (!rc && j->n_bases >= kTrimMinBases) rc = handle_trim(hh);  // big buffers back to the device pool
   if (rc && hh) {
     kmc_close(hh);
     hh = nullptr;
