@@ -665,17 +665,26 @@ def _served_run(kmc, reqs, svc, plain, rho, rng, local_rank, pos, mem_budget):
             except Exception:
                 pass
 
-    def collect():  # waits for the jobs in submission order and releases each at once
+    import concurrent.futures as cf
+
+    def check(i):  # compares job i with the serial result and releases it
+        kms, cnt, lat[i] = kmc.kmc_server_result(s, ids[i], copy=False)
+        same[i] = digest(kms, cnt) == plain[i]
+        del kms, cnt
+        kmc.kmc_server_release(s, ids[i])
+        got[0] += 1
+
+    def collect():  # waits for the jobs in submission order; checks run on 4 threads
         try:
-            for i in range(len(reqs)):
-                have.acquire()
-                if not kmc.kmc_server_wait(s, ids[i], 600.0):
-                    raise TimeoutError(f"request {i} not done after 600 s")
-                kms, cnt, lat[i] = kmc.kmc_server_result(s, ids[i], copy=False)
-                same[i] = digest(kms, cnt) == plain[i]
-                del kms, cnt
-                kmc.kmc_server_release(s, ids[i])
-                got[0] += 1
+            with cf.ThreadPoolExecutor(max_workers=4) as ex:
+                futs = []
+                for i in range(len(reqs)):
+                    have.acquire()
+                    if not kmc.kmc_server_wait(s, ids[i], 600.0):
+                        raise TimeoutError(f"request {i} not done after 600 s")
+                    futs.append(ex.submit(check, i))
+                for f in futs:
+                    f.result()
         except Exception as e:  # reported below
             err.append(f"{type(e).__name__}: {e}")
 

@@ -74,6 +74,7 @@ struct ResultPool {
       if (best < free.size()) {
         *out = free[best];
         free.erase(free.begin() + (long)best);
+        kept -= out->cap * 12;
         return KMC_OK;
       }
     }
@@ -91,10 +92,23 @@ struct ResultPool {
     *out = Buf{static_cast<uint64_t *>(k), static_cast<uint32_t *>(c), cap};
     return KMC_OK;
   }
+  // Buffers given back are kept for reuse up to kKeepBytes in all; beyond
+  // that they are freed, so that the pool does not keep the host memory of a
+  // burst of large results.
+  static constexpr uint64_t kKeepBytes = 8ull << 30;
+  uint64_t kept = 0;
   void give(uint64_t *k, uint32_t *c, uint64_t cap) {
     if (!k) return;
-    std::lock_guard<std::mutex> g(mu);
-    free.push_back(Buf{k, c, cap});
+    {
+      std::lock_guard<std::mutex> g(mu);
+      if (kept + cap * 12 <= kKeepBytes) {
+        free.push_back(Buf{k, c, cap});
+        kept += cap * 12;
+        return;
+      }
+    }
+    cudaFreeHost(k);
+    cudaFreeHost(c);
   }
   ~ResultPool() {
     for (Buf &b : free) {
